@@ -1,0 +1,89 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle source (CPU only), compiles it,
+and runs the pins of test_oracle_pins against it: at least one pin must fail.  This is
+the evidence that the pins constrain every term of the step, not just the happy path.
+"""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+# (name, text in dem_oracle.c, replacement, pins expected to notice)
+MUTANTS = [
+    ("normal stiffness factor", "double kn = 4.0 / 3.0 * Ye * sq;", "double kn = 1.0 * Ye * sq;",
+     ["test_static_overlap_on_plane_matches_hertz"]),
+    ("Young mixing ignores the wall",
+     "  double Yw = eff_young(&c->particle, &c->wall);", "  double Yw = eff_young(&c->particle, &c->particle);",
+     ["test_static_overlap_on_plane_matches_hertz"]),
+    ("effective mass of a pair", "double me = 1.0 / (1.0 / s->m[i] + 1.0 / s->m[j]);",
+     "double me = s->m[i];", [("test_restitution_recovers_input_coefficient", dict(e=0.7, v_rel=1.0))]),
+    ("effective radius of a pair", "double Re = 1.0 / (1.0 / s->R[i] + 1.0 / s->R[j]);",
+     "double Re = s->R[i];", ["test_hertz_head_on_contact_time_and_depth"]),
+    ("normal damping factor", "double eta_n = -2.0 * sqrt(5.0 / 6.0) * beta * sqrt(Sn * me);",
+     "double eta_n = -2.0 * beta * sqrt(Sn * me);", ["test_restitution_on_wall"]),
+    ("beta without pi", "return le / sqrt(le * le + ORC_PI * ORC_PI);", "return le / sqrt(le * le + 1.0);",
+     ["test_restitution_on_wall"]),
+    ("tangential stiffness factor", "double kt = 8.0 * Ge * sq;", "double kt = 4.0 * Ge * sq;",
+     ["test_tangential_stiffness_mindlin_with_rolling_coupling"]),
+    ("shear-modulus mixing", "return 1.0 / (2.0 * (2.0 - a->poisson) * (1.0 + a->poisson) / a->young +",
+     "return 1.0 / (1.0 * (2.0 - a->poisson) * (1.0 + a->poisson) / a->young +",
+     ["test_tangential_stiffness_mindlin_with_rolling_coupling"]),
+    ("tangential damping dropped", "o->Ft[d] = -(kt * dt_t[d]) - eta_t * vrt[d];",
+     "o->Ft[d] = -(kt * dt_t[d]);", ["test_tangential_damping_decay_rate"]),
+    ("moment of inertia factor", "s->I[i] = 0.4 * s->m[i] * R * R;", "s->I[i] = 0.5 * s->m[i] * R * R;",
+     ["test_sliding_then_rolling_five_sevenths", "test_tangential_stiffness_mindlin_with_rolling_coupling"]),
+    ("tangential torque sign (walls)", "s->M[3 * i + d] += s->R[i] * o.nxFt[d] + o.Mr[d];\n      }\n    }\n  }",
+     "s->M[3 * i + d] += -s->R[i] * o.nxFt[d] + o.Mr[d];\n      }\n    }\n  }",
+     ["test_sliding_then_rolling_five_sevenths"]),
+    ("tangential overlap update sign", "dt_t[d] = dt_t[d] + vrt[d] * dt;", "dt_t[d] = dt_t[d] - vrt[d] * dt;",
+     ["test_tangential_stiffness_mindlin_with_rolling_coupling", "test_sliding_then_rolling_five_sevenths"]),
+    ("rotation term of the contact velocity", "vij[d] = (s->v[3 * i + d] - Vw[d]) + rwxn[d];",
+     "vij[d] = (s->v[3 * i + d] - Vw[d]) - rwxn[d];", ["test_sliding_then_rolling_five_sevenths"]),
+    ("Coulomb limit keeps the overlap", "      dt_t[d] = (o->Ft[d] + eta_t * vrt[d]) / (-kt);\n", "",
+     ["test_coulomb_limit_invariant_and_continuity", "test_sliding_then_rolling_five_sevenths"]),
+    ("Coulomb overlap without the damping correction",
+     "dt_t[d] = (o->Ft[d] + eta_t * vrt[d]) / (-kt);", "dt_t[d] = (o->Ft[d]) / (-kt);",
+     ["test_coulomb_limit_invariant_and_continuity"]),
+    ("rolling torque dropped", "if (rolling == 1 && adw > 0.0)", "if (rolling == 7 && adw > 0.0)",
+     ["test_rolling_resistance_deceleration"]),
+    ("wall spin ignored in rolling", "dw[d] = s->w[3 * i + d] - Om[d];", "dw[d] = s->w[3 * i + d];",
+     ["test_turntable_spin_up_by_rolling_torque"]),
+    ("wall surface velocity reversed", "cross3(Om, arm, Vw);", "cross3(arm, Om, Vw);",
+     ["test_turntable_spin_up_by_rolling_torque", "test_cylinder_static_overlap_and_drum_drag"]),
+    ("translation of the wall ignored", "Vw[d] += W->velocity[d];", "Vw[d] += 0.0;",
+     ["test_translating_plate_drags_sphere_to_two_sevenths"]),
+    ("reaction on j missing", "s->F[3 * j + d] -= f;", "s->F[3 * j + d] -= 0.5 * f;",
+     ["test_momentum_conserved_by_pair_forces"]),
+    ("Euler drift instead of Verlet", "double h = 0.5 * c->dt;", "double h = 0.0 * c->dt;",
+     ["test_free_fall_is_exact"]),
+    ("search threshold not strict", "if (sqdist(&s->x[3 * i], &s->x[3 * j]) < rc2) {",
+     "if (sqdist(&s->x[3 * i], &s->x[3 * j]) <= rc2) {", [("test_cell_search_equals_brute_force", dict(seed=1))]),
+    ("search misses diagonal cells", "for (int dz = -1; dz <= 1; dz++)", "for (int dz = 0; dz <= 1; dz++)",
+     [("test_cell_search_equals_brute_force", dict(seed=1))]),
+    ("floating wall never switches off", "int on = s->active[i] && t >= W->t_on && t < W->t_off;",
+     "int on = s->active[i] && t >= W->t_on;", ["test_floating_wall_holds_until_t_off"]),
+    ("cylinder overlap sign", "double ov = R - (W->radius - rho);", "double ov = R - (rho - W->radius);",
+     ["test_cylinder_static_overlap_and_drum_drag"]),
+    ("annulus rim ignored", "if (rho < W->inner_radius || rho > W->radius) {", "if (rho > W->radius) {",
+     ["test_annulus_face_and_rim_contact_geometry"]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,tests", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_kill_mutant(name, old, new, tests, tmp_path):
+    src = oracle.source()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    lib = oracle.compile_variant(src.replace(old, new), os.path.join(str(tmp_path), "mut.so"))
+    failed = []
+    with oracle.swap_library(lib):
+        for t in tests:
+            name_t, kw = (t, {}) if isinstance(t, str) else t
+            fn = getattr(pins, name_t)
+            try:
+                fn(**kw)
+            except (AssertionError, ValueError, RuntimeError, FloatingPointError):
+                failed.append(t)
+    assert failed, f"mutant '{name}' survived {tests}"
