@@ -1,0 +1,408 @@
+"""Benchmark of the GB300 DEM hot path: particle-steps per second and HBM roofline.
+
+Default workload (N = 1): the 4.3M-sphere flat-bottomed cylindrical silo (d = 5 mm,
+R = 0.5 m, orifice 0.05 m plugged by a floating wall), as a packed bed in which every
+sphere touches its lattice neighbours, mixed precision (FP32 contact forces, FP64 state),
+dt = 1e-5 s, skin 0.5 d.  Synthetic, seeded, generated on the host; no data files.
+
+One "step" is one DEM time step of the whole system: rebuild decision, contact search
+when due (cell sort, fine search, history remap), forces with history, integration.
+
+Outputs one JSON line (rank 0).  Keys beyond the contract:
+  fp64      -- the plain FP64 GPU path on the same workload (the "mixed vs FP64" of the metric)
+  roofline  -- the step kernel against measured HBM bandwidth, from CUDA events around
+               its launches (dem_step_profiled) and the run's own contact counts
+  cpu_baseline -- the CPU oracle on a bounded sample of the same workload
+
+--impl reference times the CPU oracle (the only reference implementation there is) on a
+bounded sample of the same workload.
+Multi-GPU (torchrun): each rank advances its own replica (weak scaling, no collective in
+the data path); timing is barrier-bracketed and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DEM particle-steps/s on 1 GB300 (mixed vs FP64 plain), % of HBM roofline"
+UNIT = "particle-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+STEP_KERNEL_SOURCES = ["paper_2106_09576_gb300/csrc/dem_step_impl.cuh", "paper_2106_09576_gb300/csrc/dem_step_mixed.cu",
+                       "paper_2106_09576_gb300/csrc/dem_device.cuh"]
+REBUILD_KERNELS = 13   # kernels launched by one contact search (plus one memset)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["silo", "drum"], default="silo")
+    p.add_argument("--n", type=int, default=None, help="override the particle count (smaller runs)")
+    p.add_argument("--fp64-steps", type=int, default=None)
+    p.add_argument("--profile-steps", type=int, default=None)
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def make_workload(name, n=None, precision="mixed"):
+    import workloads
+    if name == "silo":
+        wl = workloads.silo(n=n or 4_300_000, precision=precision, spacing=0.995, jitter=0.002)
+        desc = "silo-packed"
+    else:
+        wl = workloads.drum(n=n or 200_000, precision=precision, spacing=0.999)
+        desc = "drum-rotating"
+    return wl, desc
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sources_sha():
+    h = hashlib.sha256()
+    for rel in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_desc, n):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = sources_sha()
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 5 and not line.startswith("#") and f[0] == "k_step_mixed" and f[1] == workload_desc \
+                and f[2] == sha:
+            per_particle = float(f[3]) / float(f[4])
+            return per_particle * n
+    return None
+
+
+def algorithmic_bytes(st, n_active):
+    """Bytes the method must move per force-and-integration launch: read x, v, w (FP64)
+    and the radius (FP32), write x, v, w, read x_ref: 172 B per particle; 4 B per listed
+    pair (one index), 48 B per touching pair and per particle-wall contact (FP64 tangential
+    overlap read and written)."""
+    return (172.0 * n_active + 4.0 * st["n_pairs"] + 48.0 * st["n_touch"] + 48.0 * st["n_wall_touch"])
+
+
+def dist_setup(gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_rate(wl, seconds, max_steps=None, warmup=0):
+    """Times the CPU oracle on a bounded sample of the workload: a central vertical column
+    of the silo (or a central slab of the drum) sized so the run takes about `seconds`."""
+    import oracle
+    import workloads
+    x = wl.x
+    # probe speed on a small column, then size the sample
+    def column(k_target):
+        r2 = x[:, 0] ** 2 + x[:, 1] ** 2 if wl.name == "silo" else x[:, 0] ** 2 + (x[:, 2] + 0.0) ** 2
+        order = np.argsort(r2, kind="stable")
+        return np.sort(order[:min(k_target, wl.n)])
+
+    def sub(idx):
+        return workloads.Workload("sample", dict(wl.cfg), wl.walls, x[idx], wl.v[idx], wl.w[idx], wl.radius[idx])
+
+    probe = sub(column(4000))
+    o = oracle.OracleSim(probe.cfg, probe.x, probe.v, probe.w, probe.radius, probe.walls)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(3)
+    rate = 3 * probe.n / (time.perf_counter() - t0)
+    o.close()
+    steps = max_steps if max_steps is not None else 5
+    k = int(max(2000, min(wl.n, rate * seconds / max(steps + warmup, 1))))
+    s = sub(column(k))
+    o = oracle.OracleSim(s.cfg, s.x, s.v, s.w, s.radius, s.walls)
+    o.step(max(warmup, 1))                         # first search and force evaluation untimed
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    o.close()
+    return s.n * steps / dt, s.n, steps, dt
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, desc = make_workload(args.workload, args.n, "mixed")
+    budget = 120.0
+    rate, k, steps, dt = oracle_rate(wl, budget, max_steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "gpu_launches": 0,
+        "config": {"workload": f"{desc}-{wl.n}", "sample": k, "parallelism": "single-thread CPU"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{k} spheres of the {desc} workload (central column), {steps} steps"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    from paper_2106_09576_gb300 import DEM
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl, desc = make_workload(args.workload, args.n, "mixed")
+    n = wl.n
+    extra = {}
+
+    # ---------------- mixed precision, device-resident inputs, graph path
+    g = DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="mixed", device=dev)
+    g.step(args.warmup)
+    g.sync()
+    st0 = g.stats()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    st1 = g.stats()
+    ms_max = max_over_ranks(ms, world)
+    active = 0.5 * (st0["n_active"] + st1["n_active"])
+    psteps = sum_over_ranks(active * args.steps, world)
+    value = psteps / (ms_max / 1e3)
+    rebuilds = st1["rebuilds"] - st0["rebuilds"]
+    launches = 1 + 2 * args.steps + REBUILD_KERNELS * rebuilds
+
+    # ---------------- step-kernel roofline (CUDA events around each launch)
+    kp = args.profile_steps if args.profile_steps is not None else min(args.steps, 200)
+    prof = g.step_profiled(kp)
+    st2 = g.stats()
+    kernel_ms = prof["step_kernel_ms"] / max(prof["step_launches"], 1)
+    alg = algorithmic_bytes(st2, st2["n_active"])
+    peak, peak_src = measured_hbm_peak()
+    achieved = alg / (kernel_ms / 1e3) / 1e9
+    traffic = recorded_traffic(desc, st2["n_active"])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_step<mixed>", "peak_source": peak_src,
+                "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": alg,
+                "bytes_per_particle_step": alg / max(st2["n_active"], 1),
+                "search_ms_avg": prof["search_ms"] / max(prof["searches"], 1), "searches": prof["searches"],
+                "profiled_steps": kp, "step_share_of_time": prof["step_kernel_ms"] /
+                max(prof["step_kernel_ms"] + prof["search_ms"], 1e-12)}
+    contacts = {"n_pairs": st2["n_pairs"], "n_touch": st2["n_touch"], "n_wall_touch": st2["n_wall_touch"],
+                "rebuilds_in_window": rebuilds, "max_overlap_ratio": st2["max_overlap_ratio"]}
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        x_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        v_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        w_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+        a_h = torch.empty((n,), dtype=torch.uint8, pin_memory=True)
+        g.state((x_h, v_h, w_h, a_h))
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.set_state(x_h, v_h, w_h, a_h)          # host -> device
+        g.step(args.steps)
+        g.state((x_h, v_h, w_h, a_h))            # device -> host (synchronises)
+        t_e2e = time.perf_counter() - t0
+        barrier(world)
+        t_e2e = max_over_ranks(t_e2e, world)
+        st3 = g.stats()
+        e2e_val = sum_over_ranks(st3["n_active"] * args.steps, world) / t_e2e
+        bytes_io = n * (3 * 3 * 8 + 1)
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io / args.steps,
+               "d2h_bytes_per_step": bytes_io / args.steps, "steps_per_call": args.steps,
+               "note": "dem_set_state(host) + dem_step(steps) + dem_get_state(host), pinned host memory"}
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+
+    # ---------------- plain FP64 on the same workload
+    if not args.no_fp64:
+        kf = args.fp64_steps if args.fp64_steps is not None else max(10, min(args.steps, 100))
+        gf = DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="fp64", device=dev)
+        gf.step(args.warmup)
+        gf.sync()
+        s0 = gf.stats()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        gf.step(kf)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = max_over_ranks(f0.elapsed_time(f1), world)
+        s1 = gf.stats()
+        fv = sum_over_ranks(0.5 * (s0["n_active"] + s1["n_active"]) * kf, world) / (fms / 1e3)
+        extra["fp64"] = {"value": fv, "unit": UNIT, "steps": kf, "ms_per_step": fms / kf,
+                         "mixed_speedup": value / fv}
+        gf.close()
+        del gf
+        torch.cuda.empty_cache()
+
+    # ---------------- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if not args.no_cpu and world == 1 and rank == 0:
+        rate, k, steps, dt = oracle_rate(wl, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{k} spheres of the {desc} workload (central column), {steps} steps, "
+                         f"{dt:.1f} s, single thread, host CPU of the GPU box"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{desc}-{n}", "n": n, "precision": "mixed", "dt": wl.cfg["dt"],
+                       "d": float(2 * wl.radius.max()), "skin": wl.cfg.get("skin", 0.0),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (state + lists + overlaps > 129 MB)"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck,
+            "contacts": contacts,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

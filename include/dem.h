@@ -68,6 +68,9 @@ typedef struct {
 typedef struct {
   int64_t n;                 /* particles, 0 < n < 2^31 */
   double density;            /* kg/m^3; m = density * 4/3 pi R^3, I = 2/5 m R^2 */
+  double radius_max;         /* largest particle radius; d_max = 2 radius_max sets the search
+                                threshold and the cell grid (dem_create checks every radius
+                                is <= radius_max) */
   dem_material particle;     /* particle-particle contacts use this material */
   dem_material wall;         /* particle-wall contacts: Y_e, G_e mix both; e, mu, mu_r of the wall */
   double gravity[3];         /* m/s^2 */
@@ -143,6 +146,15 @@ dem_status dem_set_walls(dem_ctx* ctx, const dem_wall* walls, int32_t n_walls);
 /* Advances n_steps >= 0 time steps, asynchronously on the context's stream.  Returns
  * DEM_ERR_STATE if a sticky device error is already known on the host. */
 dem_status dem_step(dem_ctx* ctx, int64_t n_steps);
+
+/* Measurement entry point: advances n_steps >= 0 time steps with the same kernels as
+ * dem_step, but launched one by one on the context's stream, with CUDA events around
+ * every launch of the force-and-integration kernel and around every contact search; the
+ * host waits for each step's search decision.  Outputs (any may be NULL): summed device
+ * milliseconds of the step kernel and of the searches, the number of step-kernel
+ * launches and of searches.  Synchronises. */
+dem_status dem_step_profiled(dem_ctx* ctx, int64_t n_steps, double* step_kernel_ms, double* search_ms,
+                             int64_t* step_launches, int64_t* searches);
 
 /* Blocks until the context's stream is idle; reports sticky device errors. */
 dem_status dem_sync(dem_ctx* ctx);

@@ -118,6 +118,7 @@ def _bind(lib):
     lib.orc_get_state.argtypes = [P, P, P, P, P]
     lib.orc_set_state.argtypes = [P, P, P, P, P]
     lib.orc_get_forces.argtypes = [P, P, P]
+    lib.orc_get_force_scales.argtypes = [P, P, P]
     lib.orc_get_pairs.restype = C.c_int64
     lib.orc_get_pairs.argtypes = [P, P, C.c_int64]
     lib.orc_get_history.restype = C.c_int64
@@ -229,6 +230,12 @@ class OracleSim:
         F = np.empty((self.n, 3)); M = np.empty((self.n, 3))
         self.lib.orc_get_forces(self.h, _ptr(F), _ptr(M))
         return F, M
+
+    def force_scales(self):
+        """Per particle: sum of |contact force| and of |contact torque| (error scales)."""
+        Fa = np.empty(self.n); Ma = np.empty(self.n)
+        self.lib.orc_get_force_scales(self.h, _ptr(Fa), _ptr(Ma))
+        return Fa, Ma
 
     def pairs(self) -> np.ndarray:
         cnt = self.lib.orc_get_pairs(self.h, None, 0)

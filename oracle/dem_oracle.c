@@ -45,6 +45,7 @@ struct orc_sim {
   int64_t n;
   double *x, *v, *w;       /* [n][3] */
   double *F, *M;           /* [n][3] contact force / torque sums of the last evaluation */
+  double *Fabs, *Mabs;     /* [n] sums of |contact force| and |contact torque| (error scales) */
   double *R, *m, *I;       /* radius, mass, moment of inertia */
   uint8_t* active;
   double* xref;            /* positions at the last contact search */
@@ -361,6 +362,8 @@ static void evaluate_forces(orc_sim* s, int incr) {
   int64_t n = s->n;
   memset(s->F, 0, sizeof(double) * 3 * n);
   memset(s->M, 0, sizeof(double) * 3 * n);
+  memset(s->Fabs, 0, sizeof(double) * n);
+  memset(s->Mabs, 0, sizeof(double) * n);
   double Ye = eff_young(&c->particle, &c->particle);
   double Ge = eff_shear(&c->particle, &c->particle);
   double beta = damping_beta(c->particle.restitution);
@@ -404,6 +407,14 @@ static void evaluate_forces(orc_sim* s, int incr) {
       s->M[3 * i + d] += s->R[i] * o.nxFt[d] + o.Mr[d];
       s->M[3 * j + d] += s->R[j] * o.nxFt[d] - o.Mr[d];
     }
+    {
+      double f[3] = {o.Fn[0] + o.Ft[0], o.Fn[1] + o.Ft[1], o.Fn[2] + o.Ft[2]};
+      double af = norm3(f), at = norm3(o.nxFt), ar = norm3(o.Mr);
+      s->Fabs[i] += af;
+      s->Fabs[j] += af;
+      s->Mabs[i] += s->R[i] * at + ar;
+      s->Mabs[j] += s->R[j] * at + ar;
+    }
   }
   /* particle-wall contacts */
   double Yw = eff_young(&c->particle, &c->wall);
@@ -440,6 +451,11 @@ static void evaluate_forces(orc_sim* s, int incr) {
       for (int d = 0; d < 3; d++) {
         s->F[3 * i + d] += o.Fn[d] + o.Ft[d];
         s->M[3 * i + d] += s->R[i] * o.nxFt[d] + o.Mr[d];
+      }
+      {
+        double f[3] = {o.Fn[0] + o.Ft[0], o.Fn[1] + o.Ft[1], o.Fn[2] + o.Ft[2]};
+        s->Fabs[i] += norm3(f);
+        s->Mabs[i] += s->R[i] * norm3(o.nxFt) + norm3(o.Mr);
       }
     }
   }
@@ -505,6 +521,8 @@ orc_sim* orc_create(const orc_config* cfg, const double* x, const double* v, con
   s->w = (double*)malloc(sizeof(double) * 3 * n1);
   s->F = (double*)calloc((size_t)(3 * n1), sizeof(double));
   s->M = (double*)calloc((size_t)(3 * n1), sizeof(double));
+  s->Fabs = (double*)calloc((size_t)n1, sizeof(double));
+  s->Mabs = (double*)calloc((size_t)n1, sizeof(double));
   s->xref = (double*)malloc(sizeof(double) * 3 * n1);
   s->R = (double*)malloc(sizeof(double) * n1);
   s->m = (double*)malloc(sizeof(double) * n1);
@@ -538,6 +556,7 @@ orc_sim* orc_create(const orc_config* cfg, const double* x, const double* v, con
 void orc_destroy(orc_sim* s) {
   if (!s) return;
   free(s->x); free(s->v); free(s->w); free(s->F); free(s->M); free(s->xref);
+  free(s->Fabs); free(s->Mabs);
   free(s->R); free(s->m); free(s->I); free(s->active); free(s->Hw);
   free(s->pi); free(s->pj); free(s->H);
   free(s);
@@ -592,6 +611,14 @@ int orc_get_forces(orc_sim* s, double* F, double* M) {
   ensure_forces(s);
   if (F) memcpy(F, s->F, sizeof(double) * 3 * s->n);
   if (M) memcpy(M, s->M, sizeof(double) * 3 * s->n);
+  return 0;
+}
+
+int orc_get_force_scales(orc_sim* s, double* Fabs, double* Mabs) {
+  if (!s) return 1;
+  ensure_forces(s);
+  if (Fabs) memcpy(Fabs, s->Fabs, sizeof(double) * s->n);
+  if (Mabs) memcpy(Mabs, s->Mabs, sizeof(double) * s->n);
   return 0;
 }
 

@@ -73,6 +73,9 @@ int orc_set_state(orc_sim* s, const double* x, const double* v, const double* w,
                   const uint8_t* active);
 /* Contact force and torque sums (gravity excluded) of the last force evaluation. */
 int orc_get_forces(orc_sim* s, double* F, double* M);
+/* Per particle: sum over its contacts of |F_n + F_t| and of |R n x F_t| + |M_r| in the
+ * last force evaluation (scales for relative error measures). */
+int orc_get_force_scales(orc_sim* s, double* Fabs, double* Mabs);
 /* Current fine-search list as (i, j) pairs with i < j, lexicographic order. */
 int64_t orc_get_pairs(orc_sim* s, int32_t* pairs, int64_t cap);
 /* Pairs with non-zero tangential overlap (i < j, delta_t of the (i,j) orientation),

@@ -1,0 +1,228 @@
+// dem_device.cuh -- device-side data layout and helpers of the GB300 DEM hot path.
+//
+// Layout in HBM (all inside the caller's workspace; see dem_api.cu for the offsets):
+//   per particle, cell-sorted order, structure of arrays
+//     x[2], v[2], w[2]  FP64 [3][n]   ping-pong by time step (parity ctl->cur)
+//     act[2]            uint8 [n]     1 = in the system; ping-pong with the state
+//     rad[2], id[2]     FP32 / int32  reordered at each rebuild (parity ctl->sbuf)
+//     xref              FP64 [3][n]   positions at the last contact search
+//     mask[2]           uint64 [n]    bit k < 56: neighbour slot k has a tangential overlap;
+//                                     bit 56+w: wall w has one (parity ctl->hc)
+//     hist[2]           FP64 [n][32][3] tangential overlaps of the set bits, compact, in
+//                                     bit order (parity ctl->hc)
+//     nbr               int32 [n][56] fine-search list (full list: each pair twice)
+//     nbr_cnt           int32 [n]
+//   per cell: cell_count, cell_start (int32 [n_cells + 2])
+//   hash table of tangential overlaps used at rebuild: hkey uint64 [cap], hval FP64 [cap][3]
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace demgb {
+
+constexpr int kMaxWalls = 8;
+constexpr int kMaxNbr = 56;      // slots per particle in the fine-search list
+constexpr int kHistStride = 32;  // simultaneous contacts per particle (particles + walls)
+constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
+
+// status bits (sticky, in Control::status)
+constexpr unsigned kStCapacity = 1u, kStNonfinite = 2u, kStOverlap = 4u, kStTimeout = 8u;
+
+struct WallDev {
+  int kind;
+  int pad;
+  double p[3];      // point (plane), point on axis (cylinder), centre (annulus)
+  double n[3];      // unit normal / axis
+  double radius, inner;
+  double Om[3];     // angular velocity vector of the surface
+  double c[3];      // rotation origin
+  double V[3];      // translation velocity of the surface
+  double t_on, t_off;
+};
+
+// Device-resident control block: everything that changes from step to step.
+struct Control {
+  int cur;              // state parity holding the positions of the next force evaluation
+  int sbuf;             // parity of rad/id (flips at rebuild)
+  int hc;               // parity of mask/hist
+  int need_rebuild;     // set by the step kernel when a displacement exceeds skin/2
+  int init;             // 1: the next evaluation is the initial one (no overlap increment)
+  int ran;              // 1: at least one evaluation has run since the state was set
+  int last;             // 1: the current evaluation is the last of a dem_step call
+  int hist_preloaded;   // 1: the hash table already holds overlaps given by the caller
+  int n_act_sorted;     // particles [0, n_act_sorted) were active at the last rebuild
+  int max_nbr_seen;
+  int do_rebuild;       // decision of the current iteration (read by the host in eager mode)
+  unsigned blocks_done; // step-kernel blocks finished (the last one flips the parities)
+  unsigned status;      // sticky error bits
+  unsigned max_ovl_bits;  // float bits of max delta_n / R over the last step
+  long long step;       // completed time steps
+  long long since_rebuild;
+  long long rebuilds;
+  long long remaining;  // evaluations left in the current dem_step call
+  unsigned long long n_touch_dir;   // directed particle-particle contacts, last step
+  unsigned long long n_wall_touch;
+  unsigned long long n_pairs_dir;   // directed fine-search entries at the last rebuild
+  unsigned long long n_active;
+  unsigned long long n_active_now;  // scratch of dem_get_stats
+};
+
+struct Params {
+  int n;
+  int n_walls;
+  int precision;        // 0 FP64, 1 mixed
+  int rolling;          // 0 none, 1 constant
+  int rebuild_every;
+  int nc[3];
+  int n_cells;
+  unsigned hcap_mask;   // hash capacity - 1 (power of two)
+  double dt, half_dt;
+  double g[3];
+  double density;
+  double rc2;           // fine-search threshold squared
+  double disp_lim2;     // (skin/2)^2
+  double z_sink;
+  double max_overlap_ratio;
+  double lo[3], inv_h[3];
+  float wall_margin;    // FP32 prefilter margin for walls (m)
+  // material constants (Table equation_parameters): effective Y and G, -2 sqrt(5/6) beta
+  double Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp;
+  double Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
+  WallDev walls[kMaxWalls];
+  // buffers
+  double* x[2];
+  double* v[2];
+  double* w[2];
+  uint8_t* act[2];
+  float* rad[2];
+  int* id[2];
+  unsigned long long* mask[2];
+  double* hist[2];
+  double* xref;
+  int* nbr;
+  int* nbr_cnt;
+  unsigned* key;        // [n] cell key of the current (pre-sort) order
+  int* local;           // [n] slot within the cell
+  int* order;           // [n] sorted position -> previous position
+  int* cell_count;      // [n_cells + 1]
+  int* cell_start;      // [n_cells + 2]
+  int* scan_tmp;        // block sums of the scan
+  unsigned long long* hkey;
+  double* hval;         // [cap][3]
+  double* wall_tmp;     // [n][kMaxWalls][3] wall overlaps by particle id, at rebuild
+  uint8_t* wall_tmp_mask;  // [n]
+  double* out_v;        // [3][n] full-step velocities of the last step (sorted order)
+  double* out_w;
+  double* out_F;        // [3][n] contact force and torque sums of the last evaluation
+  double* out_M;
+  double* stage;        // [9][n] staging in caller order for state transfers
+  Control* ctl;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+
+// Squared distance dx*dx + dy*dy + dz*dz with dx = b - a, left to right, no contraction:
+// the same rounding as the CPU reference of the contact search.
+__device__ __forceinline__ double sqdist_exact(double ax, double ay, double az, double bx, double by,
+                                               double bz) {
+  double dx = dsub(bx, ax), dy = dsub(by, ay), dz = dsub(bz, az);
+  double s = dmul(dx, dx);
+  s = dadd(s, dmul(dy, dy));
+  s = dadd(s, dmul(dz, dz));
+  return s;
+}
+
+// Error-free transformations in FP32 (Knuth two-sum, FMA two-product).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// FP32 -> FP64 conversion with integer operations (exact for normal numbers; zero and
+// subnormals map to signed zero; inf/NaN preserved).  Keeps conversions off the FP64
+// pipe, which on this part issues at 1/72 of the FP32 rate.
+__device__ __forceinline__ double f2d_int(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned sign = u & 0x80000000u;
+  unsigned e = (u >> 23) & 0xFFu;
+  unsigned m = u & 0x7FFFFFu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3);
+  unsigned lo = m << 29;
+  hi = (e == 0u) ? sign : hi;
+  lo = (e == 0u) ? 0u : lo;
+  hi = (e == 255u) ? (sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u)) : hi;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// FP64 -> FP32 with integer operations, rounding half away from zero on the magnitude;
+// results below the FP32 normal range flush to zero, above it saturate to infinity.
+__device__ __forceinline__ float d2f_int(double d) {
+  unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  unsigned sign = hi & 0x80000000u;
+  int e = (int)((hi >> 20) & 0x7FFu) - 896;
+  unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  unsigned r = ((unsigned)(e > 0 ? e : 0) << 23) + m + ((lo >> 28) & 1u);
+  r = (e <= 0) ? 0u : r;
+  r = (e >= 255 || r >= 0x7F800000u) ? 0x7F800000u : r;
+  return __uint_as_float(r | sign);
+}
+
+// Split x into hi + lo (FP32 each) with integer operations: hi keeps the leading 24
+// significant bits of x (truncated), lo the next 24 (rounded); |x - hi - lo| <= 2^-48 |x|.
+// Values below 2^-75 in magnitude collapse to (0, 0).
+__device__ __forceinline__ void split_df(double x, float& h, float& l) {
+  unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  unsigned sign = hw & 0x80000000u;
+  int e = (int)((hw >> 20) & 0x7FFu);
+  int ef = e - 896;
+  unsigned mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  float hv = __uint_as_float(sign | ((unsigned)(ef > 0 ? ef : 0) << 23) | mh);
+  unsigned ml = lw & 0x1FFFFFFFu;
+  float scale = __uint_as_float((unsigned)(e > 948 ? e - 948 : 0) << 23);
+  float lv = __fmul_rn(__uint2float_rn(ml), scale);
+  lv = sign ? -lv : lv;
+  bool ok = (ef > 0) && (ef < 255);
+  h = ok ? hv : (ef >= 255 ? __double2float_rn(x) : 0.0f);
+  l = ok ? lv : 0.0f;
+}
+
+// b - a as an unevaluated FP32 pair (s, t), exact up to the rounding of the low parts.
+__device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, float& s, float& t) {
+  float e;
+  two_sum(bh, -ah, s, e);
+  t = __fadd_rn(__fsub_rn(bl, al), e);
+}
+
+__device__ __forceinline__ unsigned long long pair_key(int a, int b) {
+  unsigned lo = (unsigned)(a < b ? a : b), hi = (unsigned)(a < b ? b : a);
+  return ((unsigned long long)lo << 32) | hi;
+}
+__device__ __forceinline__ unsigned hash_slot(unsigned long long k, unsigned mask) {
+  unsigned long long h = k * 0x9E3779B97F4A7C15ull;
+  return (unsigned)(h >> 32) & mask;
+}
+
+__device__ __forceinline__ int cell_coord(double xd, double lo, double inv_h, int nc) {
+  double f = floor(dmul(dsub(xd, lo), inv_h));
+  // NaN and negative map to 0, beyond the grid to the last cell
+  return (f >= 0.0) ? (f < (double)nc ? (int)f : nc - 1) : 0;
+}
+
+// Launchers (host side), defined in the .cu files.
+void launch_rebuild(const Params& P, cudaStream_t s);
+void launch_hist_clear(const Params& P, cudaStream_t s, int force);
+void scan_exclusive_i32(const int* in, int n, int* out, int* partials, cudaStream_t s);
+void launch_step_fp64(const Params& P, cudaStream_t s);
+void launch_step_mixed(const Params& P, cudaStream_t s);
+
+constexpr int kStepBlock = 128;
+
+}  // namespace demgb

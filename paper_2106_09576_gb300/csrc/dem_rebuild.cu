@@ -1,0 +1,394 @@
+// dem_rebuild.cu -- contact search at a rebuild step (Sec. 3.1-3.2).
+//
+// Sequence (all on the context stream, inside a conditional graph node):
+//   1. save the tangential overlaps of the old list into a hash table keyed by the
+//      caller ids (id_min, id_max); particle-wall overlaps go to a per-id scratch;
+//   2. cell key of every active particle over a uniform grid (cell edge >= r_c);
+//      counting sort by key: per-cell counts (integer atomics), exclusive scan (the
+//      cell ranges), scatter, then each cell's members ordered by previous position,
+//      so the result is a stable sort and does not depend on atomic order;
+//   3. permute the particle state into the other buffer (x_ref = x);
+//   4. fine search: for each particle, the 27 cells sharing a vertex with its own
+//      (the broad search), keep j with |x_j - x_i|^2 < r_c^2 (same rounding as the CPU
+//      reference), and order the list by partner id;
+//   5. for every new list entry look the pair up in the hash table and rebuild the
+//      compact per-particle overlap storage and its bit mask.
+#include "dem_device.cuh"
+
+namespace demgb {
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+// ------------------------------------------------------------------ exclusive scan
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int warp_sums[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    warp_sums[lane] = s;
+  }
+  __syncthreads();
+  int excl = x - v + (wid > 0 ? warp_sums[wid - 1] : 0);
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return excl;
+}
+
+__global__ void k_scan_partials(const int* in, int n, int* partials) {
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int s = 0;
+  for (int k = 0; k < kScanItems; k++) s += (base + k < n) ? in[base + k] : 0;
+  int total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+__global__ void k_scan_partials_top(int* partials, int nb) {
+  // one block; nb <= kScanTile
+  int base = threadIdx.x * kScanItems;
+  int vals[kScanItems];
+  int s = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    vals[k] = (base + k < nb) ? partials[base + k] : 0;
+    s += vals[k];
+  }
+  int excl = block_exclusive_scan(s, nullptr);
+  for (int k = 0; k < kScanItems; k++) {
+    if (base + k < nb) partials[base + k] = excl;
+    excl += vals[k];
+  }
+}
+
+// out[0..n] = exclusive scan of in[0..n-1]; out[n] = total
+__global__ void k_scan_final(const int* in, int n, const int* partials, int* out) {
+  int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int vals[kScanItems];
+  int s = 0;
+  for (int k = 0; k < kScanItems; k++) {
+    vals[k] = (base + k < n) ? in[base + k] : 0;
+    s += vals[k];
+  }
+  int total;
+  int excl = block_exclusive_scan(s, &total) + partials[blockIdx.x];
+  for (int k = 0; k < kScanItems; k++) {
+    if (base + k < n) out[base + k] = excl;
+    excl += vals[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partials[blockIdx.x] + total;
+}
+
+void scan_exclusive_i32(const int* in, int n, int* out, int* partials, cudaStream_t s) {
+  int nb = (n + kScanTile - 1) / kScanTile;
+  if (nb < 1) nb = 1;
+  k_scan_partials<<<nb, kScanBlock, 0, s>>>(in, n, partials);
+  k_scan_partials_top<<<1, kScanBlock, 0, s>>>(partials, nb);
+  k_scan_final<<<nb, kScanBlock, 0, s>>>(in, n, partials, out);
+}
+
+// ------------------------------------------------------------------ 1. save history
+__global__ void k_hist_save(Params P) {
+  const Control* C = P.ctl;
+  if (C->hist_preloaded) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= C->n_act_sorted) return;
+  const int cur = C->cur, sb = C->sbuf, hc = C->hc;
+  if (!P.act[cur][i]) return;
+  const unsigned long long m = P.mask[hc][i];
+  if (!m) return;
+  const int* ids = P.id[sb];
+  const int a = ids[i];
+  const double* H = P.hist[hc] + (size_t)i * kHistStride * 3;
+  const int* nb = P.nbr + (size_t)i * kMaxNbr;
+  int rank = 0;
+  for (int k = 0; k < 64; k++) {
+    if (!((m >> k) & 1ull)) continue;
+    if (k < kMaxNbr) {
+      const int b = ids[nb[k]];
+      if (a < b) {  // each unordered pair stored once, orientation (a, b)
+        const unsigned long long key = pair_key(a, b);
+        unsigned h = hash_slot(key, P.hcap_mask);
+        bool done = false;
+        for (unsigned probe = 0; probe <= P.hcap_mask; probe++) {
+          unsigned long long prev = atomicCAS(&P.hkey[h], kEmptyKey, key);
+          if (prev == kEmptyKey || prev == key) {
+            P.hval[3 * (size_t)h] = H[3 * rank];
+            P.hval[3 * (size_t)h + 1] = H[3 * rank + 1];
+            P.hval[3 * (size_t)h + 2] = H[3 * rank + 2];
+            done = true;
+            break;
+          }
+          h = (h + 1) & P.hcap_mask;
+        }
+        if (!done) atomicOr(&P.ctl->status, kStCapacity);
+      }
+    } else {
+      const int w = k - kMaxNbr;
+      double* dst = P.wall_tmp + ((size_t)a * kMaxWalls + w) * 3;
+      dst[0] = H[3 * rank];
+      dst[1] = H[3 * rank + 1];
+      dst[2] = H[3 * rank + 2];
+      P.wall_tmp_mask[a] |= (uint8_t)(1u << w);
+    }
+    rank++;
+  }
+}
+
+// ------------------------------------------------------------------ 2. cell sort
+__global__ void k_cell_count(Params P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  const int cur = P.ctl->cur;
+  const double* X = P.x[cur];
+  const int n = P.n;
+  unsigned key;
+  if (P.act[cur][p]) {
+    int cx = cell_coord(X[p], P.lo[0], P.inv_h[0], P.nc[0]);
+    int cy = cell_coord(X[n + p], P.lo[1], P.inv_h[1], P.nc[1]);
+    int cz = cell_coord(X[2 * n + p], P.lo[2], P.inv_h[2], P.nc[2]);
+    key = (unsigned)((cz * P.nc[1] + cy) * P.nc[0] + cx);
+  } else {
+    key = (unsigned)P.n_cells;  // bucket of particles that left the system
+  }
+  P.key[p] = key;
+  P.local[p] = atomicAdd(&P.cell_count[key], 1);
+}
+
+__global__ void k_cell_scatter(Params P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  P.order[P.cell_start[P.key[p]] + P.local[p]] = p;
+}
+
+// Orders each cell's members by previous position: the sort becomes stable and
+// independent of the order in which the atomics were served.
+__global__ void k_cell_order(Params P) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= P.n_cells) return;  // the out-of-system bucket keeps any order
+  const int b = P.cell_start[c], e = P.cell_start[c + 1];
+  for (int a = b + 1; a < e; a++) {
+    int v = P.order[a];
+    int k = a - 1;
+    while (k >= b && P.order[k] > v) {
+      P.order[k + 1] = P.order[k];
+      k--;
+    }
+    P.order[k + 1] = v;
+  }
+}
+
+// ------------------------------------------------------------------ 3. permute
+__global__ void k_permute(Params P) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n;
+  if (q >= n) return;
+  const Control* C = P.ctl;
+  const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf;
+  const int p = P.order[q];
+  const int nact = P.cell_start[P.n_cells];
+  const uint8_t a = P.act[cur][p];
+  for (int d = 0; d < 3; d++) {
+    const double xv = P.x[cur][d * n + p], vv = P.v[cur][d * n + p], wv = P.w[cur][d * n + p];
+    P.x[nxt][d * n + q] = xv;
+    P.v[nxt][d * n + q] = vv;
+    P.w[nxt][d * n + q] = wv;
+    P.xref[d * n + q] = xv;
+    if (q >= nact) {  // particles out of the system are never touched by the step kernel
+      P.x[cur][d * n + q] = xv;
+      P.v[cur][d * n + q] = vv;
+      P.w[cur][d * n + q] = wv;
+    }
+  }
+  P.act[nxt][q] = a;
+  if (q >= nact) P.act[cur][q] = a;
+  P.rad[sb ^ 1][q] = P.rad[sb][p];
+  P.id[sb ^ 1][q] = P.id[sb][p];
+}
+
+// ------------------------------------------------------------------ 4. fine search
+__global__ void k_neighbors(Params P) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n;
+  const int nact = P.cell_start[P.n_cells];
+  if (q >= nact) {
+    if (q < n) P.nbr_cnt[q] = 0;
+    return;
+  }
+  const int nxt = P.ctl->cur ^ 1, sb1 = P.ctl->sbuf ^ 1;
+  const double* X = P.x[nxt];
+  const int* ids = P.id[sb1];
+  const double xi = X[q], yi = X[n + q], zi = X[2 * n + q];
+  const int cx = cell_coord(xi, P.lo[0], P.inv_h[0], P.nc[0]);
+  const int cy = cell_coord(yi, P.lo[1], P.inv_h[1], P.nc[1]);
+  const int cz = cell_coord(zi, P.lo[2], P.inv_h[2], P.nc[2]);
+  int* out = P.nbr + (size_t)q * kMaxNbr;
+  int cnt = 0;
+  bool overflow = false;
+  for (int dz = -1; dz <= 1; dz++) {
+    const int z = cz + dz;
+    if (z < 0 || z >= P.nc[2]) continue;
+    for (int dy = -1; dy <= 1; dy++) {
+      const int y = cy + dy;
+      if (y < 0 || y >= P.nc[1]) continue;
+      for (int dx = -1; dx <= 1; dx++) {
+        const int x = cx + dx;
+        if (x < 0 || x >= P.nc[0]) continue;
+        const int c = (z * P.nc[1] + y) * P.nc[0] + x;
+        const int b = P.cell_start[c], e = P.cell_start[c + 1];
+        for (int j = b; j < e; j++) {
+          if (j == q) continue;
+          if (sqdist_exact(xi, yi, zi, X[j], X[n + j], X[2 * n + j]) < P.rc2) {
+            if (cnt < kMaxNbr) {
+              // insertion by partner id keeps the list ordered as a serial pair loop
+              const int idj = ids[j];
+              int k = cnt - 1;
+              while (k >= 0 && ids[out[k]] > idj) {
+                out[k + 1] = out[k];
+                k--;
+              }
+              out[k + 1] = j;
+              cnt++;
+            } else {
+              overflow = true;
+            }
+          }
+        }
+      }
+    }
+  }
+  P.nbr_cnt[q] = cnt;
+  if (overflow) atomicOr(&P.ctl->status, kStCapacity);
+  atomicMax(&P.ctl->max_nbr_seen, cnt + (overflow ? 1 : 0));
+  atomicAdd(&P.ctl->n_pairs_dir, (unsigned long long)cnt);
+}
+
+// ------------------------------------------------------------------ 5. restore history
+__global__ void k_hist_load(Params P) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n;
+  if (q >= n) return;
+  const Control* C = P.ctl;
+  const int nact = P.cell_start[P.n_cells];
+  const int hn = C->hc ^ 1, sb1 = C->sbuf ^ 1;
+  if (q >= nact) {
+    P.mask[0][q] = 0ull;
+    P.mask[1][q] = 0ull;
+    return;
+  }
+  const int* ids = P.id[sb1];
+  const int a = ids[q];
+  const int* nb = P.nbr + (size_t)q * kMaxNbr;
+  const int cnt = P.nbr_cnt[q];
+  double* H = P.hist[hn] + (size_t)q * kHistStride * 3;
+  unsigned long long m = 0ull;
+  int rank = 0;
+  for (int k = 0; k < cnt; k++) {
+    const int b = ids[nb[k]];
+    const unsigned long long key = pair_key(a, b);
+    unsigned h = hash_slot(key, P.hcap_mask);
+    for (unsigned probe = 0; probe <= P.hcap_mask; probe++) {
+      const unsigned long long kk = P.hkey[h];
+      if (kk == kEmptyKey) break;
+      if (kk == key) {
+        if (rank < kHistStride) {
+          const double sg = a < b ? 1.0 : -1.0;
+          H[3 * rank] = sg * P.hval[3 * (size_t)h];
+          H[3 * rank + 1] = sg * P.hval[3 * (size_t)h + 1];
+          H[3 * rank + 2] = sg * P.hval[3 * (size_t)h + 2];
+          m |= 1ull << k;
+          rank++;
+        } else {
+          atomicOr(&P.ctl->status, kStCapacity);
+        }
+        break;
+      }
+      h = (h + 1) & P.hcap_mask;
+    }
+  }
+  const uint8_t wm = P.wall_tmp_mask[a];
+  for (int w = 0; w < kMaxWalls; w++) {
+    if (!((wm >> w) & 1u)) continue;
+    if (rank < kHistStride) {
+      const double* src = P.wall_tmp + ((size_t)a * kMaxWalls + w) * 3;
+      H[3 * rank] = src[0];
+      H[3 * rank + 1] = src[1];
+      H[3 * rank + 2] = src[2];
+      m |= 1ull << (kMaxNbr + w);
+      rank++;
+    } else {
+      atomicOr(&P.ctl->status, kStCapacity);
+    }
+  }
+  P.mask[hn][q] = m;
+}
+
+__global__ void k_rebuild_begin(Params P) {
+  Control* C = P.ctl;
+  C->max_nbr_seen = 0;
+  C->n_pairs_dir = 0ull;
+}
+
+__global__ void k_rebuild_end(Params P) {
+  Control* C = P.ctl;
+  C->cur ^= 1;
+  C->sbuf ^= 1;
+  C->hc ^= 1;
+  C->n_act_sorted = P.cell_start[P.n_cells];
+  C->need_rebuild = 0;
+  C->since_rebuild = 0;
+  C->rebuilds++;
+  C->hist_preloaded = 0;
+}
+
+// Clearing of the hash table and the wall scratch runs before k_hist_save; it is
+// separate so that dem_set_history can clear, then fill, then mark them preloaded.
+__global__ void k_hist_clear(Params P, int force) {
+  if (!force && P.ctl->hist_preloaded) return;
+  const size_t cap = (size_t)P.hcap_mask + 1;
+  for (size_t h = blockIdx.x * (size_t)blockDim.x + threadIdx.x; h < cap; h += (size_t)gridDim.x * blockDim.x)
+    P.hkey[h] = kEmptyKey;
+  for (size_t a = blockIdx.x * (size_t)blockDim.x + threadIdx.x; a < (size_t)P.n;
+       a += (size_t)gridDim.x * blockDim.x)
+    P.wall_tmp_mask[a] = 0;
+}
+
+void launch_hist_clear(const Params& P, cudaStream_t s, int force) {
+  k_hist_clear<<<152 * 8, 256, 0, s>>>(P, force);
+}
+
+void launch_rebuild(const Params& P, cudaStream_t s) {
+  const int T = 256;
+  const int nb = (P.n + T - 1) / T;
+  k_rebuild_begin<<<1, 1, 0, s>>>(P);
+  // 1. the hash table and the wall scratch are cleared unless the caller preloaded them
+  //    (dem_set_history clears and fills them itself and sets hist_preloaded)
+  launch_hist_clear(P, s, 0);
+  k_hist_save<<<nb, T, 0, s>>>(P);
+  // 2. counting sort by cell key
+  cudaMemsetAsync(P.cell_count, 0, sizeof(int) * (P.n_cells + 1), s);
+  k_cell_count<<<nb, T, 0, s>>>(P);
+  scan_exclusive_i32(P.cell_count, P.n_cells + 1, P.cell_start, P.scan_tmp, s);
+  k_cell_scatter<<<nb, T, 0, s>>>(P);
+  k_cell_order<<<(P.n_cells + 1 + T - 1) / T, T, 0, s>>>(P);
+  // 3. permutation
+  k_permute<<<nb, T, 0, s>>>(P);
+  // 4. fine search
+  k_neighbors<<<nb, T, 0, s>>>(P);
+  // 5. history
+  k_hist_load<<<nb, T, 0, s>>>(P);
+  k_rebuild_end<<<1, 1, 0, s>>>(P);
+}
+
+}  // namespace demgb

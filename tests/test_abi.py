@@ -1,0 +1,129 @@
+"""The C ABI library builds, loads, exports every declared entry point, and its ctypes
+mirror has the same struct layout as include/dem.h.  No GPU is needed: only host-side
+entry points (workspace sizing, argument validation, status strings) are called."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2106_09576_gb300 import build as B
+from paper_2106_09576_gb300 import dem as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dem.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return D.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dem_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (dem_[a-z_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+    assert sorted(D.EXPORTED) == names
+
+
+LAYOUT_PROG = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "dem.h"
+#define F(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
+int main(void) {
+  printf("dem_config %zu\ndem_wall %zu\ndem_stats %zu\ndem_material %zu\n", sizeof(dem_config),
+         sizeof(dem_wall), sizeof(dem_stats), sizeof(dem_material));
+  F(dem_config, radius_max) F(dem_config, gravity) F(dem_config, rebuild_every)
+  F(dem_config, domain_lo) F(dem_config, z_sink) F(dem_config, max_overlap_ratio)
+  F(dem_wall, point) F(dem_wall, radius) F(dem_wall, omega) F(dem_wall, t_off)
+  F(dem_stats, time) F(dem_stats, status_bits) F(dem_stats, required_workspace)
+  return 0;
+}
+"""
+
+
+def test_ctypes_layout_matches_header(tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text(LAYOUT_PROG)
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(got["dem_config"]) == C.sizeof(D.Config)
+    assert int(got["dem_wall"]) == C.sizeof(D.Wall)
+    assert int(got["dem_stats"]) == C.sizeof(D.Stats)
+    assert int(got["dem_material"]) == C.sizeof(D.Material)
+    for key, val in got.items():
+        if "." not in key:
+            continue
+        T, f = key.split(".")
+        cls = {"dem_config": D.Config, "dem_wall": D.Wall, "dem_stats": D.Stats}[T]
+        assert getattr(cls, f).offset == int(val), key
+
+
+def cfg_dict(**kw):
+    m = dict(young=1e7, poisson=0.3, restitution=0.9, mu_slide=0.3, mu_roll=0.1)
+    c = dict(density=2500.0, particle=m, wall=dict(m), gravity=(0, 0, -9.81), dt=1e-5,
+             domain_lo=(0, 0, 0), domain_hi=(0.1, 0.1, 0.1))
+    c.update(kw)
+    return c
+
+
+def test_workspace_bytes_and_validation(lib):
+    size = C.c_size_t(0)
+    cfg = D.make_config(cfg_dict(), 1000, 1.5e-3)
+    assert lib.dem_workspace_bytes(C.byref(cfg), C.byref(size)) == 0
+    assert size.value > 1000 * 100
+    big = D.make_config(cfg_dict(), 4_300_000, 2.5e-3)
+    s2 = C.c_size_t(0)
+    assert lib.dem_workspace_bytes(C.byref(big), C.byref(s2)) == 0
+    assert s2.value > size.value
+    for bad in (dict(dt=0.0), dict(density=-1.0), dict(domain_hi=(0, 0.1, 0.1))):
+        c = D.make_config(cfg_dict(**bad), 1000, 1.5e-3)
+        assert lib.dem_workspace_bytes(C.byref(c), C.byref(size)) == 1
+    c = D.make_config(cfg_dict(), 0, 1.5e-3)
+    assert lib.dem_workspace_bytes(C.byref(c), C.byref(size)) == 1
+    c = D.make_config(cfg_dict(), 10, 1.5e-3, precision=3)
+    assert lib.dem_workspace_bytes(C.byref(c), C.byref(size)) == 1
+    bad_mat = cfg_dict()
+    bad_mat["particle"] = dict(bad_mat["particle"], restitution=0.0)
+    c = D.make_config(bad_mat, 10, 1.5e-3)
+    assert lib.dem_workspace_bytes(C.byref(c), C.byref(size)) == 1
+
+
+def test_create_rejects_null_arguments_without_touching_the_device(lib):
+    cfg = D.make_config(cfg_dict(), 10, 1.5e-3)
+    h = C.c_void_p()
+    assert lib.dem_create(C.byref(cfg), None, None, None, None, None, 0, None, C.byref(h)) == 1
+    assert lib.dem_step(None, 1) == 1
+    assert lib.dem_get_stats(None, None) == 1
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.dem_status_string(code)
+    assert b"unknown" in lib.dem_status_string(99)
+
+
+def test_product_path_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2106_09576_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "dem_oracle" not in text, f

@@ -35,8 +35,8 @@ MUTANTS = [
      "o->Ft[d] = -(kt * dt_t[d]);", ["test_tangential_damping_decay_rate"]),
     ("moment of inertia factor", "s->I[i] = 0.4 * s->m[i] * R * R;", "s->I[i] = 0.5 * s->m[i] * R * R;",
      ["test_sliding_then_rolling_five_sevenths", "test_tangential_stiffness_mindlin_with_rolling_coupling"]),
-    ("tangential torque sign (walls)", "s->M[3 * i + d] += s->R[i] * o.nxFt[d] + o.Mr[d];\n      }\n    }\n  }",
-     "s->M[3 * i + d] += -s->R[i] * o.nxFt[d] + o.Mr[d];\n      }\n    }\n  }",
+    ("tangential torque sign (walls)", "s->M[3 * i + d] += s->R[i] * o.nxFt[d] + o.Mr[d];\n      }\n      {\n        double f[3]",
+     "s->M[3 * i + d] += -s->R[i] * o.nxFt[d] + o.Mr[d];\n      }\n      {\n        double f[3]",
      ["test_sliding_then_rolling_five_sevenths"]),
     ("tangential overlap update sign", "dt_t[d] = dt_t[d] + vrt[d] * dt;", "dt_t[d] = dt_t[d] - vrt[d] * dt;",
      ["test_tangential_stiffness_mindlin_with_rolling_coupling", "test_sliding_then_rolling_five_sevenths"]),

@@ -181,7 +181,7 @@ def _fcc(a: float, lo, hi):
 
 def drum(n: int = 200_000, seed: int | None = None, rmin: float = 1.5e-3, rmax: float = 2.5e-3,
          omega: float = 1.0, precision: str = "fp64", fill_scale: float | None = None,
-         mu_slide: float = 0.3, restitution: float = 0.9) -> Workload:
+         mu_slide: float = 0.3, restitution: float = 0.9, spacing: float = 1.02) -> Workload:
     """Rotating drum, horizontal axis along y, polydisperse spheres on an FCC lattice.
 
     The drum keeps the aspect L/R = 0.1/0.12 of the rotating-drum case and is sized so
@@ -197,7 +197,7 @@ def drum(n: int = 200_000, seed: int | None = None, rmin: float = 1.5e-3, rmax: 
         R *= fill_scale
     L = aspect * R
     dmax = 2.0 * rmax
-    a = 1.02 * dmax
+    a = spacing * dmax
     pts = _fcc(a, (-R, 0.0, -R), (R, L, R))
     rho = np.hypot(pts[:, 0], pts[:, 2])
     inside = (rho < R - 0.55 * dmax) & (pts[:, 1] > 0.55 * dmax) & (pts[:, 1] < L - 0.55 * dmax)
@@ -220,28 +220,30 @@ def drum(n: int = 200_000, seed: int | None = None, rmin: float = 1.5e-3, rmax: 
 
 def silo(n: int = 4_300_000, seed: int | None = None, d: float = 5e-3, R: float = 0.5,
          orifice: float = 0.05, height: float = 1.0, t_open: float = 1e300,
-         precision: str = "mixed") -> Workload:
+         precision: str = "mixed", spacing: float = 1.1, jitter: float = 0.025) -> Workload:
     """Flat-bottomed cylindrical silo: cylinder wall, annular bottom with a central
-    orifice, a floating plug over the orifice until t_open; simple cubic fill at 1.1 d
-    with jitter <= 0.025 d.  Search with a skin of 0.5 d (r_c = 1.5 d), rebuilt when a
-    displacement exceeds 0.25 d; particles are removed 0.1 m below the orifice."""
+    orifice, a floating plug over the orifice until t_open; simple cubic fill at
+    `spacing` d with jitter <= `jitter` d (1.1 and 0.025: a loose fill that falls and
+    packs; 0.995 and 0.002: a packed bed in which every sphere touches its lattice
+    neighbours).  Search with a skin of 0.5 d (r_c = 1.5 d), rebuilt when a displacement
+    exceeds 0.25 d; particles are removed 0.1 m below the orifice."""
     rng = np.random.Generator(np.random.PCG64(seed_for(3) if seed is None else seed))
     r = 0.5 * d
-    a = 1.1 * d
+    a = spacing * d
     m = int(math.floor((2 * (R - r)) / a))
     coords = (np.arange(m) - (m - 1) / 2.0) * a
     X, Y = np.meshgrid(coords, coords, indexing="ij")
     X, Y = X.ravel(), Y.ravel()
-    keep = np.hypot(X, Y) < R - r - 0.05 * d
+    keep = np.hypot(X, Y) < R - r - max(0.05 * d, 2 * jitter * d)
     X, Y = X[keep], Y[keep]
     per_layer = len(X)
     layers = int(math.ceil(n / per_layer))
-    Z = r + 0.05 * d + np.arange(layers) * a
+    Z = r + max(0.05 * d, 2 * jitter * d) + np.arange(layers) * a
     x = np.empty((layers * per_layer, 3))
     x[:, 0] = np.tile(X, layers)
     x[:, 1] = np.tile(Y, layers)
     x[:, 2] = np.repeat(Z, per_layer)
-    x = x[:n] + rng.uniform(-0.025, 0.025, (n, 3)) * d
+    x = x[:n] + rng.uniform(-jitter, jitter, (n, 3)) * d
     top = max(height, float(x[:, 2].max()) + 2 * d)
     walls = [cylinder((0, 0, 0), (0, 0, 1), R),
              annulus((0, 0, 0), (0, 0, 1), R, orifice),
