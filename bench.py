@@ -39,9 +39,9 @@ sys.path.insert(0, ROOT)
 METRIC = "DEM particle-steps/s on 1 GB300 (mixed vs FP64 plain), % of HBM roofline"
 UNIT = "particle-steps/s"
 FALLBACK_HBM_GBS = 6800.0
-STEP_KERNEL_SOURCES = ["paper_2106_09576_gb300/csrc/dem_step_impl.cuh", "paper_2106_09576_gb300/csrc/dem_step_mixed.cu",
+STEP_KERNEL_SOURCES = ["paper_2106_09576_gb300/csrc/dem_step_common.cuh", "paper_2106_09576_gb300/csrc/dem_step_mixed.cu",
                        "paper_2106_09576_gb300/csrc/dem_device.cuh"]
-REBUILD_KERNELS = 13   # kernels launched by one contact search (plus one memset)
+REBUILD_KERNELS = 14   # kernels launched by one contact search (plus one memset)
 
 
 def parse():
@@ -310,7 +310,7 @@ def run_ours(args):
     achieved = alg / (kernel_ms / 1e3) / 1e9
     traffic = recorded_traffic(desc, st2["n_active"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_step<mixed>", "peak_source": peak_src,
+                "traffic": traffic, "kernel": "k_step_mixed", "peak_source": peak_src,
                 "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": alg,
                 "bytes_per_particle_step": alg / max(st2["n_active"], 1),
                 "search_ms_avg": prof["search_ms"] / max(prof["searches"], 1), "searches": prof["searches"],

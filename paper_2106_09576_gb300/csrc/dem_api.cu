@@ -172,6 +172,12 @@ __global__ void k_begin(Params P, cudaGraphConditionalHandle h_loop, cudaGraphCo
                        ? 1
                        : 0;
   C->do_rebuild = need;
+  // walls present at the time of this evaluation (floating walls, Sec. 3.6)
+  const double t = (double)C->step * P.dt;
+  unsigned on = 0u;
+  for (int k = 0; k < P.n_walls; k++)
+    if (t >= P.walls[k].t_on && t < P.walls[k].t_off) on |= 1u << k;
+  C->wall_on = on;
   C->n_touch_dir = 0ull;
   C->n_wall_touch = 0ull;
   C->n_active = 0ull;
@@ -433,6 +439,13 @@ void fill_walls(dem_ctx* c) {
     W.inner = s.inner_radius;
     W.t_on = s.t_on;
     W.t_off = s.t_off;
+    WallF& F = c->P.wf[k];
+    for (int d = 0; d < 3; d++) {
+      F.p[d] = (float)W.p[d];
+      F.n[d] = (float)W.n[d];
+    }
+    F.radius = (float)W.radius;
+    F.inner = (float)W.inner;
   }
   c->P.n_walls = c->n_walls;
 }
@@ -672,6 +685,26 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   P.ceta_pw = eta_coeff(cfg->wall.restitution);
   P.mu_pw = cfg->wall.mu_slide;
   P.mur_pw = cfg->wall.mu_roll;
+  P.f_density = (float)P.density;
+  P.f_dt = (float)P.dt;
+  for (int a = 0; a < 3; a++) P.f_g[a] = (float)P.g[a];
+  P.f_disp_lim2 = (float)(P.disp_lim2 * (1.0 - 1e-5));   // conservative: rebuild slightly early
+  P.f_Ye_pp = (float)P.Ye_pp;
+  P.f_Ge_pp = (float)P.Ge_pp;
+  P.f_ceta_pp = (float)P.ceta_pp;
+  P.f_mu_pp = (float)P.mu_pp;
+  P.f_mur_pp = (float)P.mur_pp;
+  P.f_Ye_pw = (float)P.Ye_pw;
+  P.f_Ge_pw = (float)P.Ge_pw;
+  P.f_ceta_pw = (float)P.ceta_pw;
+  P.f_mu_pw = (float)P.mu_pw;
+  P.f_mur_pw = (float)P.mur_pw;
+  {
+    long long zb;
+    double zs = cfg->z_sink;
+    std::memcpy(&zb, &zs, 8);
+    P.z_sink_key = ordered_key(zb);
+  }
   for (int b = 0; b < 2; b++) {
     P.x[b] = (double*)(base + o.x[b]);
     P.v[b] = (double*)(base + o.v[b]);

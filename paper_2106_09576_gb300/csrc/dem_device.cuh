@@ -40,6 +40,11 @@ struct WallDev {
   double t_on, t_off;
 };
 
+// FP32 copies of the wall geometry for the conservative prefilter of the mixed path.
+struct WallF {
+  float p[3], n[3], radius, inner;
+};
+
 // Device-resident control block: everything that changes from step to step.
 struct Control {
   int cur;              // state parity holding the positions of the next force evaluation
@@ -52,6 +57,7 @@ struct Control {
   int hist_preloaded;   // 1: the hash table already holds overlaps given by the caller
   int n_act_sorted;     // particles [0, n_act_sorted) were active at the last rebuild
   int max_nbr_seen;
+  unsigned wall_on;     // bit k: wall k exists at the time of the current evaluation
   int do_rebuild;       // decision of the current iteration (read by the host in eager mode)
   unsigned blocks_done; // step-kernel blocks finished (the last one flips the parities)
   unsigned status;      // sticky error bits
@@ -89,6 +95,12 @@ struct Params {
   double Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp;
   double Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
   WallDev walls[kMaxWalls];
+  // FP32 copies of uniform constants (mixed path), computed once on the host
+  float f_density, f_dt, f_g[3], f_disp_lim2;
+  float f_Ye_pp, f_Ge_pp, f_ceta_pp, f_mu_pp, f_mur_pp;
+  float f_Ye_pw, f_Ge_pw, f_ceta_pw, f_mu_pw, f_mur_pw;
+  long long z_sink_key;   // ordered-integer image of z_sink (exact comparison without FP64)
+  WallF wf[kMaxWalls];
   // buffers
   double* x[2];
   double* v[2];
@@ -199,6 +211,11 @@ __device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, 
   float e;
   two_sum(bh, -ah, s, e);
   t = __fadd_rn(__fsub_rn(bl, al), e);
+}
+
+// Monotone map of a double's bits to a signed integer (exact ordering, integer ops only).
+__host__ __device__ __forceinline__ long long ordered_key(long long bits) {
+  return bits ^ ((bits >> 63) & 0x7FFFFFFFFFFFFFFFLL);
 }
 
 __device__ __forceinline__ unsigned long long pair_key(int a, int b) {

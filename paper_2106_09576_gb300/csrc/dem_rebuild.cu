@@ -197,24 +197,32 @@ __global__ void k_permute(Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf;
   const int p = P.order[q];
-  const int nact = P.cell_start[P.n_cells];
-  const uint8_t a = P.act[cur][p];
   for (int d = 0; d < 3; d++) {
-    const double xv = P.x[cur][d * n + p], vv = P.v[cur][d * n + p], wv = P.w[cur][d * n + p];
+    const double xv = P.x[cur][d * n + p];
     P.x[nxt][d * n + q] = xv;
-    P.v[nxt][d * n + q] = vv;
-    P.w[nxt][d * n + q] = wv;
+    P.v[nxt][d * n + q] = P.v[cur][d * n + p];
+    P.w[nxt][d * n + q] = P.w[cur][d * n + p];
     P.xref[d * n + q] = xv;
-    if (q >= nact) {  // particles out of the system are never touched by the step kernel
-      P.x[cur][d * n + q] = xv;
-      P.v[cur][d * n + q] = vv;
-      P.w[cur][d * n + q] = wv;
-    }
   }
-  P.act[nxt][q] = a;
-  if (q >= nact) P.act[cur][q] = a;
+  P.act[nxt][q] = P.act[cur][p];
   P.rad[sb ^ 1][q] = P.rad[sb][p];
   P.id[sb ^ 1][q] = P.id[sb][p];
+}
+
+// Particles out of the system sit after the active ones and are never touched by the
+// step kernel: give both state buffers their values.  Separate from k_permute, whose
+// threads still read the source buffer.
+__global__ void k_mirror_inactive(Params P) {
+  const int n = P.n;
+  const int q = P.cell_start[P.n_cells] + blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int cur = P.ctl->cur, nxt = cur ^ 1;
+  for (int d = 0; d < 3; d++) {
+    P.x[cur][d * n + q] = P.x[nxt][d * n + q];
+    P.v[cur][d * n + q] = P.v[nxt][d * n + q];
+    P.w[cur][d * n + q] = P.w[nxt][d * n + q];
+  }
+  P.act[cur][q] = P.act[nxt][q];
 }
 
 // ------------------------------------------------------------------ 4. fine search
@@ -384,6 +392,7 @@ void launch_rebuild(const Params& P, cudaStream_t s) {
   k_cell_order<<<(P.n_cells + 1 + T - 1) / T, T, 0, s>>>(P);
   // 3. permutation
   k_permute<<<nb, T, 0, s>>>(P);
+  k_mirror_inactive<<<nb, T, 0, s>>>(P);
   // 4. fine search
   k_neighbors<<<nb, T, 0, s>>>(P);
   // 5. history

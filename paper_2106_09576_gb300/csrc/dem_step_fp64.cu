@@ -1,10 +1,213 @@
-// dem_step_fp64.cu -- FP64 instantiation of the step kernel.  Built with -fmad=false so
-// that every product and sum rounds separately, as in the serial CPU statement.
-#include "dem_step_impl.cuh"
+// dem_step_fp64.cu -- the FP64 step kernel (forces, history, integration), built with
+// -fmad=false so that every product and sum rounds separately.
+//
+// One thread owns one particle i of the cell-sorted order.  It walks i's fine-search list
+// (ordered by partner id), evaluates each touching contact from i's side with the same
+// operations as the serial statement of Sec. 2.1 and adds it to F_i, M_i in list order,
+// then the walls in wall order: the sums therefore run in the same order as a serial loop
+// over pairs (i < j) in id order, and each pair term from j's side is the exact negation
+// of the term from i's side.  The results are bit-identical to that serial loop.
+#include "dem_step_common.cuh"
 
 namespace demgb {
+
+__global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
+  const Control* C = P.ctl;
+  const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf, hc = C->hc;
+  const bool init = C->init != 0, last = C->last != 0;
+  const unsigned wall_on = C->wall_on;
+  const int n = P.n, nact = C->n_act_sorted;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  StepStats st = {0u, 0u, 0u, 0.0f, 0u};
+
+  if (last && i >= nact && i < n) {
+    for (int d = 0; d < 3; d++) {   // out of the system: frozen in both buffers
+      P.out_v[d * n + i] = P.v[cur][d * n + i];
+      P.out_w[d * n + i] = P.w[cur][d * n + i];
+      P.out_F[d * n + i] = 0.0;
+      P.out_M[d * n + i] = 0.0;
+    }
+  }
+  if (i < nact) {
+    const double* X = P.x[cur];
+    const double* V = P.v[cur];
+    const double* W = P.w[cur];
+    const uint8_t* A = P.act[cur];
+    const float* RAD = P.rad[sb];
+    double* Xo = P.x[nxt];
+    double* Vo = P.v[nxt];
+    double* Wo = P.w[nxt];
+    const double xi[3] = {X[i], X[n + i], X[2 * n + i]};
+    const double vi[3] = {V[i], V[n + i], V[2 * n + i]};
+    const double wi[3] = {W[i], W[n + i], W[2 * n + i]};
+    if (!A[i]) {
+      for (int d = 0; d < 3; d++) {
+        Xo[d * n + i] = xi[d];
+        Vo[d * n + i] = vi[d];
+        Wo[d * n + i] = wi[d];
+        if (last) {
+          P.out_v[d * n + i] = vi[d];
+          P.out_w[d * n + i] = wi[d];
+          P.out_F[d * n + i] = 0.0;
+          P.out_M[d * n + i] = 0.0;
+        }
+      }
+      P.act[nxt][i] = 0;
+      P.mask[hc ^ 1][i] = 0ull;
+    } else {
+      const unsigned long long mold = P.mask[hc][i];
+      const double* Hold = P.hist[hc] + (size_t)i * kHistStride * 3;
+      double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHistStride * 3;
+      const int* nb = P.nbr + (size_t)i * kMaxNbr;
+      const int cnt = P.nbr_cnt[i];
+      unsigned long long mnew = 0ull;
+      int rank = 0;
+      const double Ri = (double)RAD[i];
+      const double mi = P.density * (4.0 / 3.0) * 3.14159265358979323846 * Ri * Ri * Ri;
+      const double Ii = 0.4 * mi * Ri * Ri;
+      double F[3] = {0.0, 0.0, 0.0}, M[3] = {0.0, 0.0, 0.0};
+
+      // particle-particle contacts in partner-id order
+      for (int k = 0; k < cnt; k++) {
+        const int j = nb[k];
+        if (!A[j]) continue;
+        const double xj[3] = {X[j], X[n + j], X[2 * n + j]};
+        const double Rj = (double)RAD[j];
+        const double r = sqrt(sqdist_exact(xi[0], xi[1], xi[2], xj[0], xj[1], xj[2]));
+        const double dn = (Ri + Rj) - r;                  // Eq. deltan
+        if (!(dn > 0.0)) continue;
+        const double dx[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
+        const double nrm[3] = {dx[0] / r, dx[1] / r, dx[2] / r};   // Eq. vecn
+        const double vj[3] = {V[j], V[n + j], V[2 * n + j]};
+        const double wj[3] = {W[j], W[n + j], W[2 * n + j]};
+        double rw[3], rwxn[3], vij[3], dw[3];
+        for (int d = 0; d < 3; d++) rw[d] = Ri * wi[d] + Rj * wj[d];
+        cross3d(rw, nrm, rwxn);
+        for (int d = 0; d < 3; d++) {
+          vij[d] = (vi[d] - vj[d]) + rwxn[d];
+          dw[d] = wi[d] - wj[d];
+        }
+        const double Re = 1.0 / (1.0 / Ri + 1.0 / Rj);
+        const double mj = P.density * (4.0 / 3.0) * 3.14159265358979323846 * Rj * Rj * Rj;
+        const double me = 1.0 / (1.0 / mi + 1.0 / mj);
+        double H[3] = {0.0, 0.0, 0.0};
+        if ((mold >> k) & 1ull) {
+          const int ro = __popcll(mold & ((1ull << k) - 1ull));
+          H[0] = Hold[ro * 3];
+          H[1] = Hold[ro * 3 + 1];
+          H[2] = Hold[ro * 3 + 2];
+        }
+        double f[3], nxFt[3], Mr[3];
+        law_d(nrm, dn, vij, dw, Re, me, P.Ye_pp, P.Ge_pp, P.ceta_pp, P.mu_pp, P.mur_pp, P.rolling, P.dt, H, !init,
+              f, nxFt, Mr);
+        for (int d = 0; d < 3; d++) {
+          F[d] += f[d];
+          M[d] += Ri * nxFt[d] + Mr[d];
+        }
+        st.touch++;
+        st.max_ovl = fmaxf(st.max_ovl, (float)(dn / fmin(Ri, Rj)));
+        if (rank < kHistStride) {
+          Hnew[rank * 3] = H[0];
+          Hnew[rank * 3 + 1] = H[1];
+          Hnew[rank * 3 + 2] = H[2];
+          mnew |= 1ull << k;
+          rank++;
+        } else {
+          st.status |= kStCapacity;
+        }
+      }
+
+      // particle-wall contacts (Sec. 2.1 last paragraph; walls move per Sec. 3.6)
+      for (int k = 0; k < P.n_walls; k++) {
+        if (!((wall_on >> k) & 1u)) continue;
+        const WallDev& Wl = P.walls[k];
+        double nrm[3], dn, ps[3];
+        if (!wall_geom_d(Wl, xi, Ri, nrm, &dn, ps)) continue;
+        const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
+        double Vw[3];
+        cross3d(Wl.Om, arm, Vw);
+        for (int d = 0; d < 3; d++) Vw[d] += Wl.V[d];
+        const int bit = kMaxNbr + k;
+        double H[3] = {0.0, 0.0, 0.0};
+        if ((mold >> bit) & 1ull) {
+          const int ro = __popcll(mold & ((1ull << bit) - 1ull));
+          H[0] = Hold[ro * 3];
+          H[1] = Hold[ro * 3 + 1];
+          H[2] = Hold[ro * 3 + 2];
+        }
+        double rw[3], rwxn[3], vij[3], dw[3];
+        for (int d = 0; d < 3; d++) rw[d] = Ri * wi[d];
+        cross3d(rw, nrm, rwxn);
+        for (int d = 0; d < 3; d++) {
+          vij[d] = (vi[d] - Vw[d]) + rwxn[d];
+          dw[d] = wi[d] - Wl.Om[d];
+        }
+        double f[3], nxFt[3], Mr[3];
+        law_d(nrm, dn, vij, dw, Ri, mi, P.Ye_pw, P.Ge_pw, P.ceta_pw, P.mu_pw, P.mur_pw, P.rolling, P.dt, H, !init, f,
+              nxFt, Mr);
+        for (int d = 0; d < 3; d++) {
+          F[d] += f[d];
+          M[d] += Ri * nxFt[d] + Mr[d];
+        }
+        st.max_ovl = fmaxf(st.max_ovl, (float)(dn / Ri));
+        st.wtouch++;
+        if (rank < kHistStride) {
+          Hnew[rank * 3] = H[0];
+          Hnew[rank * 3 + 1] = H[1];
+          Hnew[rank * 3 + 2] = H[2];
+          mnew |= 1ull << bit;
+          rank++;
+        } else {
+          st.status |= kStCapacity;
+        }
+      }
+      P.mask[hc ^ 1][i] = mnew;
+
+      // velocity Verlet (Eqs. main1, main2, newvv, halfstep)
+      double xn[3], vn[3], wn[3];
+      const double h = P.half_dt;
+      for (int d = 0; d < 3; d++) {
+        const double a = F[d] / mi + P.g[d];
+        const double al = M[d] / Ii;
+        double vf = vi[d], wf = wi[d];
+        if (!init) {
+          vf = vf + a * h;
+          wf = wf + al * h;
+        }
+        if (last) {
+          P.out_v[d * n + i] = vf;
+          P.out_w[d * n + i] = wf;
+          P.out_F[d * n + i] = F[d];
+          P.out_M[d * n + i] = M[d];
+        }
+        vn[d] = vf + a * h;
+        wn[d] = wf + al * h;
+        xn[d] = xi[d] + vn[d] * P.dt;
+        Xo[d * n + i] = xn[d];
+        Vo[d * n + i] = vn[d];
+        Wo[d * n + i] = wn[d];
+      }
+      const bool alive = !below_sink(xn[2], P.z_sink_key);
+      P.act[nxt][i] = alive ? 1 : 0;
+      if (!(finite_d(xn[0]) && finite_d(xn[1]) && finite_d(xn[2]) && finite_d(vn[0]) && finite_d(vn[1]) &&
+            finite_d(vn[2])))
+        st.status |= kStNonfinite;
+      if (alive) {
+        st.active++;
+        const double xr[3] = {P.xref[i], P.xref[n + i], P.xref[2 * n + i]};
+        if (P.rebuild_every <= 0 && sqdist_exact(xr[0], xr[1], xr[2], xn[0], xn[1], xn[2]) > P.disp_lim2)
+          P.ctl->need_rebuild = 1;
+      }
+    }
+  }
+  if (P.max_overlap_ratio > 0.0 && st.max_ovl > (float)P.max_overlap_ratio) st.status |= kStOverlap;
+  block_flush(st, P.ctl);
+  finish_step(P.ctl);
+}
+
 void launch_step_fp64(const Params& P, cudaStream_t s) {
   const int blocks = (P.n + kStepBlock - 1) / kStepBlock;
-  k_step<false><<<blocks, kStepBlock, 0, s>>>(P);
+  k_step_fp64<<<blocks, kStepBlock, 0, s>>>(P);
 }
+
 }  // namespace demgb

@@ -181,7 +181,8 @@ def _fcc(a: float, lo, hi):
 
 def drum(n: int = 200_000, seed: int | None = None, rmin: float = 1.5e-3, rmax: float = 2.5e-3,
          omega: float = 1.0, precision: str = "fp64", fill_scale: float | None = None,
-         mu_slide: float = 0.3, restitution: float = 0.9, spacing: float = 1.02) -> Workload:
+         mu_slide: float = 0.3, restitution: float = 0.9, spacing: float = 1.02,
+         spin: float = 0.0) -> Workload:
     """Rotating drum, horizontal axis along y, polydisperse spheres on an FCC lattice.
 
     The drum keeps the aspect L/R = 0.1/0.12 of the rotating-drum case and is sized so
@@ -215,7 +216,8 @@ def drum(n: int = 200_000, seed: int | None = None, rmin: float = 1.5e-3, rmax: 
                     wall=dict(mat), precision=precision)
     cfg["drum_radius"] = R
     cfg["drum_length"] = L
-    return Workload("drum", cfg, walls, x, np.zeros((n, 3)), np.zeros((n, 3)), rad)
+    w = rng.normal(0.0, spin, (n, 3)) if spin > 0 else np.zeros((n, 3))
+    return Workload("drum", cfg, walls, x, np.zeros((n, 3)), w, rad)
 
 
 def silo(n: int = 4_300_000, seed: int | None = None, d: float = 5e-3, R: float = 0.5,
