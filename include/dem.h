@@ -187,6 +187,31 @@ dem_status dem_set_history(dem_ctx* ctx, int64_t n_pairs, const int32_t* pairs,
                            const double* dt_pair, const double* dt_wall);
 
 dem_status dem_get_stats(dem_ctx* ctx, dem_stats* out);
+
+/* Contact search for callers that cannot allocate device memory (an application whose
+ * memory is entirely owned by its own pool allocator, or a loop that cannot afford the
+ * device-wide synchronisation an allocation may cause).  The paper has no counterpart:
+ * this is a service of the library, not a step of the method.
+ *
+ * Finds all pairs (i, j), i < j, of active particles with |x_j - x_i|^2 < cutoff^2 --
+ * the same set, with the same rounding, as the fine search of a context with r_c =
+ * cutoff -- using no workspace: only the caller's buffers and one fixed 10 MiB scratch
+ * array that every GPU loading the library holds until the process exits.
+ *   x       device, [n][3] FP64;  active: device uint8 [n] or NULL (all active)
+ *   domain  host double[3] each: box of the cell grid (points outside are clamped)
+ *   pairs   device int32 [capacity][2]: the first min(count, capacity) pairs, ordered by
+ *           i, then by the cells sharing a vertex with i's cell
+ *   count   host: total number of pairs (the call synchronises `stream`)
+ * Limits: n <= DEM_STATIC_MAX_PARTICLES (else DEM_ERR_CAPACITY); grids finer than
+ * DEM_STATIC_MAX_CELLS cells are coarsened.  All calls share the scratch and it keeps the
+ * last call's contents (the per-cell counters are cleared by every call); calls that
+ * overlap on the GPU race and must not be issued.  The first call on a device looks up
+ * the scratch's device address on that device, so make it before any stream capture. */
+#define DEM_STATIC_MAX_PARTICLES 262144
+#define DEM_STATIC_MAX_CELLS 524288
+dem_status dem_find_pairs_static(const double* x, const uint8_t* active, int64_t n, double cutoff,
+                                 const double* domain_lo, const double* domain_hi, int32_t* pairs,
+                                 int64_t capacity, int64_t* count, void* stream);
 const char* dem_status_string(dem_status s);
 void dem_destroy(dem_ctx* ctx);
 

@@ -22,6 +22,7 @@ SOURCES = {
     "dem_rebuild.cu": [],
     "dem_step_fp64.cu": ["-fmad=false"],
     "dem_step_mixed.cu": [],
+    "dem_static_pairs.cu": [],
 }
 
 

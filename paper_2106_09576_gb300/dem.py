@@ -20,7 +20,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 EXPORTED = ["dem_workspace_bytes", "dem_create", "dem_set_walls", "dem_step", "dem_step_profiled", "dem_sync",
             "dem_get_state",
             "dem_set_state", "dem_get_forces", "dem_get_pairs", "dem_get_history", "dem_set_history",
-            "dem_get_stats", "dem_status_string", "dem_destroy"]
+            "dem_get_stats", "dem_status_string", "dem_destroy", "dem_find_pairs_static"]
 
 
 class DemError(RuntimeError):
@@ -160,6 +160,40 @@ def make_walls(walls):
         W.t_on = w.get("t_on", -1e300)
         W.t_off = w.get("t_off", 1e300)
     return arr, len(walls)
+
+
+def find_pairs_static(x, cutoff: float, domain_lo, domain_hi, active=None, capacity=None, stream=None):
+    """dem_find_pairs_static: contact search without any device allocation by the library.
+
+    For callers that cannot allocate device memory; `x` ([n, 3] float64), `active`
+    ([n] uint8, optional) are CUDA tensors.  Returns a CUDA int32 tensor [count, 2] of the
+    pairs (i < j) with |x_j - x_i| < cutoff.  The output tensor is allocated here by torch
+    on the caller's behalf; C callers pass their own buffer."""
+    import torch
+
+    lib = load_library()
+    f = lib.dem_find_pairs_static
+    if f.argtypes is None:
+        f.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.POINTER(C.c_double),
+                      C.POINTER(C.c_double), C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
+        f.restype = C.c_int32
+    n = int(x.shape[0])
+    lo = (C.c_double * 3)(*[float(v) for v in domain_lo])
+    hi = (C.c_double * 3)(*[float(v) for v in domain_hi])
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    cnt = C.c_int64(0)
+    cap = int(capacity) if capacity is not None else 0
+    out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=x.device)
+    a = None if active is None else C.c_void_p(active.data_ptr())
+    _check(lib, "dem_find_pairs_static", f(C.c_void_p(x.data_ptr()), a, n, float(cutoff), lo, hi,
+                                            C.c_void_p(out.data_ptr()), cap, C.byref(cnt),
+                                            C.c_void_p(st.cuda_stream)))
+    if capacity is None or cnt.value > cap:
+        out = torch.empty((max(cnt.value, 1), 2), dtype=torch.int32, device=x.device)
+        _check(lib, "dem_find_pairs_static", f(C.c_void_p(x.data_ptr()), a, n, float(cutoff), lo, hi,
+                                                C.c_void_p(out.data_ptr()), cnt.value, C.byref(cnt),
+                                                C.c_void_p(st.cuda_stream)))
+    return out[: cnt.value]
 
 
 def _host(a, dtype, shape):
