@@ -6,6 +6,9 @@
 //     act[2]            uint8 [n]     1 = in the system; ping-pong with the state
 //     rad[2], id[2]     FP32 / int32  reordered at each rebuild (parity ctl->sbuf)
 //     xref              FP64 [3][n]   positions at the last contact search
+//     shadow[2]         float4 [n]    hi parts of x, y, z (truncated FP32) and the radius:
+//                                     the mixed kernel's contact prefilter reads 16 bytes
+//                                     per list entry instead of three FP64 coordinates
 //     mask[2]           uint64 [n]    bit k < 56: neighbour slot k has a tangential overlap;
 //                                     bit 56+w: wall w has one (parity ctl->hc)
 //     hist[2]           FP64 [n][32][3] tangential overlaps of the set bits, compact, in
@@ -96,7 +99,7 @@ struct Params {
   double Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
   WallDev walls[kMaxWalls];
   // FP32 copies of uniform constants (mixed path), computed once on the host
-  float f_density, f_dt, f_g[3], f_disp_lim2;
+  float f_density, f_dt, f_g[3], f_disp_lim2, f_rc;
   float f_Ye_pp, f_Ge_pp, f_ceta_pp, f_mu_pp, f_mur_pp;
   float f_Ye_pw, f_Ge_pw, f_ceta_pw, f_mu_pw, f_mur_pw;
   long long z_sink_key;   // ordered-integer image of z_sink (exact comparison without FP64)
@@ -111,6 +114,7 @@ struct Params {
   unsigned long long* mask[2];
   double* hist[2];
   double* xref;
+  float4* shadow[2];    // [n] FP32 hi parts of x, y, z and the radius, ping-pong with the state
   int* nbr;
   int* nbr_cnt;
   unsigned* key;        // [n] cell key of the current (pre-sort) order
@@ -204,6 +208,13 @@ __device__ __forceinline__ void split_df(double x, float& h, float& l) {
   bool ok = (ef > 0) && (ef < 255);
   h = ok ? hv : (ef >= 255 ? __double2float_rn(x) : 0.0f);
   l = ok ? lv : 0.0f;
+}
+
+// Leading 24 significant bits of x (truncated), as split_df's hi part, integer ops only.
+__device__ __forceinline__ float hi_df(double x) {
+  float h, l;
+  split_df(x, h, l);
+  return h;
 }
 
 // b - a as an unevaluated FP32 pair (s, t), exact up to the rounding of the low parts.

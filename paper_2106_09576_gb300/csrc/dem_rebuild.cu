@@ -197,15 +197,19 @@ __global__ void k_permute(Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf;
   const int p = P.order[q];
+  float hx[3];
   for (int d = 0; d < 3; d++) {
     const double xv = P.x[cur][d * n + p];
     P.x[nxt][d * n + q] = xv;
     P.v[nxt][d * n + q] = P.v[cur][d * n + p];
     P.w[nxt][d * n + q] = P.w[cur][d * n + p];
     P.xref[d * n + q] = xv;
+    hx[d] = hi_df(xv);
   }
+  const float r = P.rad[sb][p];
+  P.shadow[nxt][q] = make_float4(hx[0], hx[1], hx[2], r);
   P.act[nxt][q] = P.act[cur][p];
-  P.rad[sb ^ 1][q] = P.rad[sb][p];
+  P.rad[sb ^ 1][q] = r;
   P.id[sb ^ 1][q] = P.id[sb][p];
 }
 
@@ -223,6 +227,7 @@ __global__ void k_mirror_inactive(Params P) {
     P.w[cur][d * n + q] = P.w[nxt][d * n + q];
   }
   P.act[cur][q] = P.act[nxt][q];
+  P.shadow[cur][q] = P.shadow[nxt][q];
 }
 
 // ------------------------------------------------------------------ 4. fine search

@@ -16,7 +16,7 @@
 
 namespace demgb {
 
-__global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(Params P) {
+__global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf, hc = C->hc;
   const bool init = C->init != 0, last = C->last != 0;
@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(Params P) {
       }
       P.act[nxt][i] = 0;
       P.mask[hc ^ 1][i] = 0ull;
+      P.shadow[nxt][i] = P.shadow[cur][i];
     } else {
       const unsigned long long mold = P.mask[hc][i];
       const double* Hold = P.hist[hc] + (size_t)i * kHistStride * 3;
@@ -80,20 +81,60 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(Params P) {
       int rank = 0;
 
       // ---------------- particle-particle contacts
-      for (int k = 0; k < cnt; k++) {
+      // (a) Prefilter on the FP32 hi parts, 8 list entries at a time: two 16-byte loads of
+      //     indices, then 8 independent 16-byte shadow loads.  hi truncates x to 24
+      //     significant bits: |x - hi| < 2^-23 |x|, so a coordinate difference of two hi
+      //     parts (partners within r_c) is off by less than 2^-23 (2 |x_i| + 2 r_c),
+      //     rounding included; the test is widened by sqrt(3) times that bound, so it
+      //     cannot drop a contact.
+      const float4* SH = P.shadow[cur];
+      const float amax = fmaxf(fmaxf(fabsf(hx[0]), fabsf(hx[1])), fabsf(hx[2]));
+      const float slack = 1.7320508f * 1.1920929e-7f * (2.0f * amax + 2.0f * P.f_rc) + 1e-30f;
+      const int4* nb4 = reinterpret_cast<const int4*>(nb);
+      unsigned long long cand = 0ull;
+      for (int k0 = 0; k0 < cnt; k0 += 8) {
+        const int4 ja = nb4[k0 >> 2], jb = nb4[(k0 >> 2) + 1];   // row has 56 slots: in bounds
+        const int js[8] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y, jb.z, jb.w};
+        float4 sh[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) sh[u] = (k0 + u < cnt) ? SH[js[u]] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+          const float ex = sh[u].x - hx[0], ey = sh[u].y - hx[1], ez = sh[u].z - hx[2];
+          const float reach = (Rif + sh[u].w + slack) * 1.000001f;
+          if (k0 + u < cnt && ex * ex + ey * ey + ez * ez < reach * reach) cand |= 1ull << (k0 + u);
+        }
+      }
+      // (b) candidates in list order; every load of a candidate is issued before any branch
+      while (cand) {
+        const int k = __ffsll((long long)cand) - 1;
+        cand &= cand - 1ull;
         const int j = nb[k];
-        if (!A[j]) continue;
+        const bool had = (mold >> k) & 1ull;
+        const int ro = __popcll(mold & ((1ull << k) - 1ull));
+        const uint8_t aj = A[j];
         const float Rjf = RAD[j];
+        double xj[3], vj[3], wjd[3];
+        for (int d = 0; d < 3; d++) {
+          xj[d] = X[(size_t)d * n + j];
+          vj[d] = V[(size_t)d * n + j];
+          wjd[d] = W[(size_t)d * n + j];
+        }
+        double H[3] = {0.0, 0.0, 0.0};
+        if (had) {
+          H[0] = Hold[ro * 3];
+          H[1] = Hold[ro * 3 + 1];
+          H[2] = Hold[ro * 3 + 2];
+        }
+        if (!aj) continue;
         float s[3], t[3], dxf[3];
         for (int d = 0; d < 3; d++) {
           float hj, lj;
-          split_df(X[(size_t)d * n + j], hj, lj);
+          split_df(xj[d], hj, lj);
           df_diff(hx[d], lx[d], hj, lj, s[d], t[d]);
           dxf[d] = s[d] + t[d];
         }
         const float S = Rif + Rjf;
-        const float r2f = dxf[0] * dxf[0] + dxf[1] * dxf[1] + dxf[2] * dxf[2];
-        if (!(r2f < S * S * 1.000001f)) continue;
         // S^2 - r^2 as an exact double-float
         float p2, pe, e, Ah, Al;
         two_prod(s[0], s[0], Ah, pe);
@@ -119,10 +160,10 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(Params P) {
         float dv[3], dw[3], wj[3];
         for (int d = 0; d < 3; d++) {
           float h, l, s1, t1;
-          split_df(V[(size_t)d * n + j], h, l);
+          split_df(vj[d], h, l);
           df_diff(h, l, vh[d], vl[d], s1, t1);
           dv[d] = s1 + t1;
-          split_df(W[(size_t)d * n + j], h, l);
+          split_df(wjd[d], h, l);
           wj[d] = h + l;
           df_diff(h, l, wh[d], wl[d], s1, t1);
           dw[d] = s1 + t1;
@@ -133,13 +174,6 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(Params P) {
         const float Re = Rif * Rjf / S;
         const float mj = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rjf * Rjf * Rjf;
         const float me = mif * mj / (mif + mj);
-        double H[3] = {0.0, 0.0, 0.0};
-        if ((mold >> k) & 1ull) {
-          const int ro = __popcll(mold & ((1ull << k) - 1ull));
-          H[0] = Hold[ro * 3];
-          H[1] = Hold[ro * 3 + 1];
-          H[2] = Hold[ro * 3 + 2];
-        }
         law_f(nrm, dn, vij, dw, Re, me, P.f_Ye_pp, P.f_Ge_pp, P.f_ceta_pp, P.f_mu_pp, P.f_mur_pp, P.rolling, dtf, H,
               !init, Rif, Ff, Mf);
         st.touch++;
@@ -231,6 +265,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(Params P) {
         P.v[nxt][d * n + i] = vn[d];
         P.w[nxt][d * n + i] = wn[d];
       }
+      P.shadow[nxt][i] = make_float4(hi_df(xn[0]), hi_df(xn[1]), hi_df(xn[2]), Rif);
       const bool alive = !below_sink(xn[2], P.z_sink_key);
       P.act[nxt][i] = alive ? 1 : 0;
       if (!(finite_d(xn[0]) && finite_d(xn[1]) && finite_d(xn[2]) && finite_d(vn[0]) && finite_d(vn[1]) &&
