@@ -21,7 +21,9 @@ SOURCES = {
     "dem_api.cu": [],
     "dem_rebuild.cu": [],
     "dem_step_fp64.cu": ["-fmad=false"],
-    "dem_step_mixed.cu": [],
+    # FP32 division and square root need not be correctly rounded in the mixed kernel;
+    # additions, multiplications and FMAs stay IEEE (the double-float arithmetic needs them)
+    "dem_step_mixed.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "dem_static_pairs.cu": [],
 }
 

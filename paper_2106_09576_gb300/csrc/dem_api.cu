@@ -110,7 +110,7 @@ dem_status derive(const dem_config* c, Derived* d) {
 }
 
 struct Offsets {
-  size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], xref, nbr, nbr_cnt, key, local, order,
+  size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], xref, nbr, nbr_cnt, key, local, order,
       cell_count, cell_start, scan_tmp, hkey, hval, wall_tmp, wall_tmp_mask, out_v, out_w, out_F, out_M,
       stage, ctl, io_cnt, io_off;
   size_t total;
@@ -130,7 +130,9 @@ Offsets layout(const dem_config* c, const Derived& d) {
     o.id[b] = L.add(n * 4);
     o.mask[b] = L.add(n * 8);
     o.hist[b] = L.add(n * kHistStride * 3 * 8);
-    o.shadow[b] = L.add(n * 16);
+    const bool mixed = c->precision == DEM_PRECISION_MIXED;   // FP32 copies for neighbours
+    o.shadow[b] = L.add(mixed ? n * 16 : 0);
+    o.render[b] = L.add(mixed ? n * 48 : 0);
   }
   o.xref = L.add(3 * n * 8);
   o.nbr = L.add(n * kMaxNbr * 4);
@@ -717,6 +719,7 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
     P.mask[b] = (unsigned long long*)(base + o.mask[b]);
     P.hist[b] = (double*)(base + o.hist[b]);
     P.shadow[b] = (float4*)(base + o.shadow[b]);
+    P.render[b] = (float4*)(base + o.render[b]);
   }
   P.xref = (double*)(base + o.xref);
   P.nbr = (int*)(base + o.nbr);

@@ -5,10 +5,13 @@
 //     x[2], v[2], w[2]  FP64 [3][n]   ping-pong by time step (parity ctl->cur)
 //     act[2]            uint8 [n]     1 = in the system; ping-pong with the state
 //     rad[2], id[2]     FP32 / int32  reordered at each rebuild (parity ctl->sbuf)
-//     xref              FP64 [3][n]   positions at the last contact search
-//     shadow[2]         float4 [n]    hi parts of x, y, z (truncated FP32) and the radius:
-//                                     the mixed kernel's contact prefilter reads 16 bytes
-//                                     per list entry instead of three FP64 coordinates
+//     xref              FP64 [3][n]   positions at the last contact search; in a mixed
+//                                     context FP32 [6][n]: their hi parts, then lo parts
+//     shadow[2]         float4 [n]    {hx, hy, hz, R} of each particle (mixed path): what
+//                                     the contact prefilter reads; ping-pong with the state
+//     render[2]         float4 [n][3] {lx, ly, lz, in-system} {vx, vy, vz, wx}
+//                                     {wy, wz, 0, 0} (mixed path): what a contact partner
+//                                     reads; x = hx + lx to 2^-48; ping-pong with the state
 //     mask[2]           uint64 [n]    bit k < 56: neighbour slot k has a tangential overlap;
 //                                     bit 56+w: wall w has one (parity ctl->hc)
 //     hist[2]           FP64 [n][32][3] tangential overlaps of the set bits, compact, in
@@ -20,6 +23,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "../../include/dem.h"
 
 namespace demgb {
 
@@ -114,7 +119,8 @@ struct Params {
   unsigned long long* mask[2];
   double* hist[2];
   double* xref;
-  float4* shadow[2];    // [n] FP32 hi parts of x, y, z and the radius, ping-pong with the state
+  float4* shadow[2];    // [n] FP32 {x_hi, R} (see the layout above)
+  float4* render[2];    // [n][3] FP32 {x_lo, flag} {v, w_x} {w_y, w_z, 0, 0}
   int* nbr;
   int* nbr_cnt;
   unsigned* key;        // [n] cell key of the current (pre-sort) order
@@ -215,6 +221,16 @@ __device__ __forceinline__ float hi_df(double x) {
   float h, l;
   split_df(x, h, l);
   return h;
+}
+
+// Writes the FP32 shadow and render of a particle from its split position (h, l),
+// velocities and radius.
+__device__ __forceinline__ void write_render(float4* sh, float4* rd, const float* h, const float* l, const double* v,
+                                            const double* w, float R, bool active) {
+  sh[0] = make_float4(h[0], h[1], h[2], R);
+  rd[0] = make_float4(l[0], l[1], l[2], active ? 1.0f : 0.0f);
+  rd[1] = make_float4(d2f_int(v[0]), d2f_int(v[1]), d2f_int(v[2]), d2f_int(w[0]));
+  rd[2] = make_float4(d2f_int(w[1]), d2f_int(w[2]), 0.0f, 0.0f);
 }
 
 // b - a as an unevaluated FP32 pair (s, t), exact up to the rounding of the low parts.

@@ -197,18 +197,30 @@ __global__ void k_permute(Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf;
   const int p = P.order[q];
-  float hx[3];
+  double xv[3], vv[3], wv[3];
   for (int d = 0; d < 3; d++) {
-    const double xv = P.x[cur][d * n + p];
-    P.x[nxt][d * n + q] = xv;
-    P.v[nxt][d * n + q] = P.v[cur][d * n + p];
-    P.w[nxt][d * n + q] = P.w[cur][d * n + p];
-    P.xref[d * n + q] = xv;
-    hx[d] = hi_df(xv);
+    xv[d] = P.x[cur][d * n + p];
+    vv[d] = P.v[cur][d * n + p];
+    wv[d] = P.w[cur][d * n + p];
+    P.x[nxt][d * n + q] = xv[d];
+    P.v[nxt][d * n + q] = vv[d];
+    P.w[nxt][d * n + q] = wv[d];
   }
   const float r = P.rad[sb][p];
-  P.shadow[nxt][q] = make_float4(hx[0], hx[1], hx[2], r);
-  P.act[nxt][q] = P.act[cur][p];
+  const uint8_t a = P.act[cur][p];
+  if (P.precision == DEM_PRECISION_MIXED) {
+    float h[3], l[3];
+    float* xr = reinterpret_cast<float*>(P.xref);
+    for (int d = 0; d < 3; d++) {
+      split_df(xv[d], h[d], l[d]);
+      xr[d * n + q] = h[d];
+      xr[(3 + d) * n + q] = l[d];
+    }
+    write_render(P.shadow[nxt] + q, P.render[nxt] + 3 * (size_t)q, h, l, vv, wv, r, a != 0);
+  } else {
+    for (int d = 0; d < 3; d++) P.xref[d * n + q] = xv[d];
+  }
+  P.act[nxt][q] = a;
   P.rad[sb ^ 1][q] = r;
   P.id[sb ^ 1][q] = P.id[sb][p];
 }
@@ -227,7 +239,10 @@ __global__ void k_mirror_inactive(Params P) {
     P.w[cur][d * n + q] = P.w[nxt][d * n + q];
   }
   P.act[cur][q] = P.act[nxt][q];
-  P.shadow[cur][q] = P.shadow[nxt][q];
+  if (P.precision == DEM_PRECISION_MIXED) {
+    P.shadow[cur][q] = P.shadow[nxt][q];
+    for (int k = 0; k < 3; k++) P.render[cur][3 * (size_t)q + k] = P.render[nxt][3 * (size_t)q + k];
+  }
 }
 
 // ------------------------------------------------------------------ 4. fine search

@@ -243,10 +243,12 @@ __device__ __forceinline__ void block_flush(const StepStats& s, Control* C) {
 }
 
 // The last block to finish flips the state and history parities and clears the
-// initial-evaluation flag: every block has read them by then.
+// initial-evaluation flag: every block has read them by then.  No fence is needed before
+// the count: the last block writes only these control words, whose old values every
+// block consumed before counting itself, and the next kernel on the stream sees all of
+// this kernel's writes.
 __device__ __forceinline__ void finish_step(Control* C) {
   __shared__ bool is_last;
-  __threadfence();
   if (threadIdx.x == 0) is_last = atomicAdd(&C->blocks_done, 1u) == gridDim.x - 1;
   __syncthreads();
   if (is_last && threadIdx.x == 0) {

@@ -4,10 +4,12 @@
 // One thread owns one particle of the cell-sorted order and walks its fine-search list.
 // FP64 instructions issue at 1/72 of the FP32 rate on this part, so the kernel keeps them
 // to the integration (9 FMAs per particle) and the tangential-overlap accumulation
-// (3 adds per contact):
-//   - relative positions and velocities come from integer splits of the FP64 values into
-//     FP32 pairs (hi + lo) and exact two-sum differences, so nearly co-located or
-//     co-moving spheres keep their relative values to ~1e-7;
+// (3 adds per contact).  Every particle publishes, once per step, FP32 copies of itself
+// for its neighbours: a 16-byte shadow {x_hi, R} that the contact prefilter reads, and a
+// 48-byte render {x_lo, in-system flag, v, w} that a contact partner reads; its own
+// thread starts from them too and reads its FP64 state only for walls and integration.
+//   - relative positions are exact two-sum differences of the hi + lo pairs, so nearly
+//     co-located spheres keep their relative position to ~1e-7;
 //   - the normal overlap is (S^2 - r^2) / (S + r) with S^2 - r^2 formed exactly as a
 //     double-float (no cancellation at small overlaps);
 //   - FP32<->FP64 conversions use integer operations; uniform constants arrive in FP32;
@@ -16,9 +18,75 @@
 
 namespace demgb {
 
-__global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
+// One particle-wall contact: FP64 geometry, FP32 law, FP64 overlap accumulation.  Few
+// particles touch a wall, so this is kept out of line: its FP64 temporaries would
+// otherwise set the register budget (and the spills) of the whole kernel.
+struct WallOut {
+  float F[3], M[3];
+  double H[3];
+  float ovl;
+  int hit;
+};
+
+__device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, int k, int i, int cur, double x0, double x1,
+                                                   double x2, float Rif, float mif, unsigned long long mold,
+                                                   const double* Hold, bool init) {
+  const Params& P = *Pp;
+  WallOut o;
+  o.hit = 0;
+  const WallDev& Wl = P.walls[k];
+  const double xi[3] = {x0, x1, x2};
+  double nrmd[3], dnd, ps[3];
+  if (!wall_geom_d(Wl, xi, (double)Rif, nrmd, &dnd, ps)) return o;
+  const int n = P.n;
+  const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
+  double Vw[3];
+  cross3d(Wl.Om, arm, Vw);
+  for (int d = 0; d < 3; d++) Vw[d] += Wl.V[d];
+  const int bit = kMaxNbr + k;
+  double H[3] = {0.0, 0.0, 0.0};
+  if ((mold >> bit) & 1ull) {
+    const int ro = __popcll(mold & ((1ull << bit) - 1ull));
+    H[0] = Hold[ro * 3];
+    H[1] = Hold[ro * 3 + 1];
+    H[2] = Hold[ro * 3 + 2];
+  }
+  const float nf[3] = {(float)nrmd[0], (float)nrmd[1], (float)nrmd[2]};
+  const float dnf = (float)dnd;
+  // v_i - V_wall(p*) and w_i - Omega as exact double-float differences
+  float dv[3], dw[3], wif[3];
+  for (int d = 0; d < 3; d++) {
+    const double vi = P.v[cur][d * n + i], wi = P.w[cur][d * n + i];
+    float ah, al, bh, bl, s1, t1;
+    split_df(vi, ah, al);
+    split_df(Vw[d], bh, bl);
+    df_diff(bh, bl, ah, al, s1, t1);
+    dv[d] = s1 + t1;
+    split_df(wi, ah, al);
+    split_df(Wl.Om[d], bh, bl);
+    df_diff(bh, bl, ah, al, s1, t1);
+    dw[d] = s1 + t1;
+    wif[d] = d2f_int(wi);
+  }
+  const float rw[3] = {Rif * wif[0], Rif * wif[1], Rif * wif[2]};
+  const float vij[3] = {dv[0] + (rw[1] * nf[2] - rw[2] * nf[1]), dv[1] + (rw[2] * nf[0] - rw[0] * nf[2]),
+                        dv[2] + (rw[0] * nf[1] - rw[1] * nf[0])};
+  float F[3] = {0.f, 0.f, 0.f}, M[3] = {0.f, 0.f, 0.f};
+  law_f(nf, dnf, vij, dw, Rif, mif, P.f_Ye_pw, P.f_Ge_pw, P.f_ceta_pw, P.f_mu_pw, P.f_mur_pw, P.rolling, P.f_dt, H,
+        !init, Rif, F, M);
+  for (int d = 0; d < 3; d++) {
+    o.F[d] = F[d];
+    o.M[d] = M[d];
+    o.H[d] = H[d];
+  }
+  o.ovl = dnf / Rif;
+  o.hit = 1;
+  return o;
+}
+
+__global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_constant__ Params P) {
   const Control* C = P.ctl;
-  const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf, hc = C->hc;
+  const int cur = C->cur, nxt = cur ^ 1, hc = C->hc;
   const bool init = C->init != 0, last = C->last != 0;
   const unsigned wall_on = C->wall_on;
   const int n = P.n, nact = C->n_act_sorted;
@@ -27,8 +95,10 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
   const double* X = P.x[cur];
   const double* V = P.v[cur];
   const double* W = P.w[cur];
-  const uint8_t* A = P.act[cur];
-  const float* RAD = P.rad[sb];
+  const float4* SH = P.shadow[cur];
+  const float4* RD = P.render[cur];
+  float4* SHo = P.shadow[nxt];
+  float4* RDo = P.render[nxt];
 
   if (last && i >= nact && i < n) {
     for (int d = 0; d < 3; d++) {   // out of the system: frozen in both buffers
@@ -39,47 +109,30 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
     }
   }
   if (i < nact) {
-    double xi[3], vi[3], wi[3];
-    for (int d = 0; d < 3; d++) {
-      xi[d] = X[d * n + i];
-      vi[d] = V[d * n + i];
-      wi[d] = W[d * n + i];
-    }
-    if (!A[i]) {
+    const float4 o0 = SH[i];
+    const float4 o1 = RD[3 * (size_t)i];
+    if (o1.w == 0.0f) {
       for (int d = 0; d < 3; d++) {
-        P.x[nxt][d * n + i] = xi[d];
-        P.v[nxt][d * n + i] = vi[d];
-        P.w[nxt][d * n + i] = wi[d];
+        const double xv = X[d * n + i], vv = V[d * n + i], wv = W[d * n + i];
+        P.x[nxt][d * n + i] = xv;
+        P.v[nxt][d * n + i] = vv;
+        P.w[nxt][d * n + i] = wv;
         if (last) {
-          P.out_v[d * n + i] = vi[d];
-          P.out_w[d * n + i] = wi[d];
+          P.out_v[d * n + i] = vv;
+          P.out_w[d * n + i] = wv;
           P.out_F[d * n + i] = 0.0;
           P.out_M[d * n + i] = 0.0;
         }
       }
       P.act[nxt][i] = 0;
       P.mask[hc ^ 1][i] = 0ull;
-      P.shadow[nxt][i] = P.shadow[cur][i];
+      SHo[i] = o0;
+      for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
     } else {
-      const unsigned long long mold = P.mask[hc][i];
-      const double* Hold = P.hist[hc] + (size_t)i * kHistStride * 3;
-      double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHistStride * 3;
       const int* nb = P.nbr + (size_t)i * kMaxNbr;
       const int cnt = P.nbr_cnt[i];
-      const float Rif = RAD[i];
-      const float mif = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rif * Rif * Rif;
-      float hx[3], lx[3], vh[3], vl[3], wh[3], wl[3];
-      for (int d = 0; d < 3; d++) {
-        split_df(xi[d], hx[d], lx[d]);
-        split_df(vi[d], vh[d], vl[d]);
-        split_df(wi[d], wh[d], wl[d]);
-      }
-      const float wif[3] = {wh[0] + wl[0], wh[1] + wl[1], wh[2] + wl[2]};
-      const float dtf = P.f_dt;
-      float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
-      unsigned long long mnew = 0ull;
-      int rank = 0;
-
+      const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o1.x, o1.y, o1.z};
+      const float Rif = o0.w;
       // ---------------- particle-particle contacts
       // (a) Prefilter on the FP32 hi parts, 8 list entries at a time: two 16-byte loads of
       //     indices, then 8 independent 16-byte shadow loads.  hi truncates x to 24
@@ -87,7 +140,6 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
       //     parts (partners within r_c) is off by less than 2^-23 (2 |x_i| + 2 r_c),
       //     rounding included; the test is widened by sqrt(3) times that bound, so it
       //     cannot drop a contact.
-      const float4* SH = P.shadow[cur];
       const float amax = fmaxf(fmaxf(fabsf(hx[0]), fabsf(hx[1])), fabsf(hx[2]));
       const float slack = 1.7320508f * 1.1920929e-7f * (2.0f * amax + 2.0f * P.f_rc) + 1e-30f;
       const int4* nb4 = reinterpret_cast<const int4*>(nb);
@@ -97,7 +149,8 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
         const int js[8] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y, jb.z, jb.w};
         float4 sh[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) sh[u] = (k0 + u < cnt) ? SH[js[u]] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+        for (int u = 0; u < 8; u++)
+          sh[u] = (k0 + u < cnt) ? SH[js[u]] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
 #pragma unroll
         for (int u = 0; u < 8; u++) {
           const float ex = sh[u].x - hx[0], ey = sh[u].y - hx[1], ez = sh[u].z - hx[2];
@@ -105,35 +158,39 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
           if (k0 + u < cnt && ex * ex + ey * ey + ez * ez < reach * reach) cand |= 1ull << (k0 + u);
         }
       }
+      const float4 o2 = RD[3 * (size_t)i + 1], o3 = RD[3 * (size_t)i + 2];
+      const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
+      const unsigned long long mold = P.mask[hc][i];
+      const double* Hold = P.hist[hc] + (size_t)i * kHistStride * 3;
+      double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHistStride * 3;
+      const float mif = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rif * Rif * Rif;
+      const float dtf = P.f_dt;
+      float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
+      unsigned long long mnew = 0ull;
+      int rank = 0;
+
       // (b) candidates in list order; every load of a candidate is issued before any branch
       while (cand) {
         const int k = __ffsll((long long)cand) - 1;
         cand &= cand - 1ull;
         const int j = nb[k];
-        const bool had = (mold >> k) & 1ull;
-        const int ro = __popcll(mold & ((1ull << k) - 1ull));
-        const uint8_t aj = A[j];
-        const float Rjf = RAD[j];
-        double xj[3], vj[3], wjd[3];
-        for (int d = 0; d < 3; d++) {
-          xj[d] = X[(size_t)d * n + j];
-          vj[d] = V[(size_t)d * n + j];
-          wjd[d] = W[(size_t)d * n + j];
-        }
+        const float4 r0 = SH[j];
+        const float4* rj = RD + 3 * (size_t)j;
+        const float4 r1 = rj[0], r2 = rj[1], r3 = rj[2];
         double H[3] = {0.0, 0.0, 0.0};
-        if (had) {
+        if ((mold >> k) & 1ull) {
+          const int ro = __popcll(mold & ((1ull << k) - 1ull));
           H[0] = Hold[ro * 3];
           H[1] = Hold[ro * 3 + 1];
           H[2] = Hold[ro * 3 + 2];
         }
-        if (!aj) continue;
+        if (r1.w == 0.0f) continue;                    // partner out of the system
+        const float Rjf = r0.w;
         float s[3], t[3], dxf[3];
-        for (int d = 0; d < 3; d++) {
-          float hj, lj;
-          split_df(xj[d], hj, lj);
-          df_diff(hx[d], lx[d], hj, lj, s[d], t[d]);
-          dxf[d] = s[d] + t[d];
-        }
+        df_diff(hx[0], lx[0], r0.x, r1.x, s[0], t[0]);
+        df_diff(hx[1], lx[1], r0.y, r1.y, s[1], t[1]);
+        df_diff(hx[2], lx[2], r0.z, r1.z, s[2], t[2]);
+        for (int d = 0; d < 3; d++) dxf[d] = s[d] + t[d];
         const float S = Rif + Rjf;
         // S^2 - r^2 as an exact double-float
         float p2, pe, e, Ah, Al;
@@ -156,18 +213,9 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
         const float dn = D / (Sh + r);                   // Eq. deltan without cancellation
         const float ir = 1.0f / r;
         const float nrm[3] = {dxf[0] * ir, dxf[1] * ir, dxf[2] * ir};   // Eq. vecn
-        // v_i - v_j and w_i - w_j as exact double-float differences
-        float dv[3], dw[3], wj[3];
-        for (int d = 0; d < 3; d++) {
-          float h, l, s1, t1;
-          split_df(vj[d], h, l);
-          df_diff(h, l, vh[d], vl[d], s1, t1);
-          dv[d] = s1 + t1;
-          split_df(wjd[d], h, l);
-          wj[d] = h + l;
-          df_diff(h, l, wh[d], wl[d], s1, t1);
-          dw[d] = s1 + t1;
-        }
+        const float wj[3] = {r2.w, r3.x, r3.y};
+        const float dv[3] = {vif[0] - r2.x, vif[1] - r2.y, vif[2] - r2.z};
+        const float dw[3] = {wif[0] - wj[0], wif[1] - wj[1], wif[2] - wj[2]};
         const float rw[3] = {Rif * wif[0] + Rjf * wj[0], Rif * wif[1] + Rjf * wj[1], Rif * wif[2] + Rjf * wj[2]};
         const float vij[3] = {dv[0] + (rw[1] * nrm[2] - rw[2] * nrm[1]), dv[1] + (rw[2] * nrm[0] - rw[0] * nrm[2]),
                               dv[2] + (rw[0] * nrm[1] - rw[1] * nrm[0])};
@@ -189,50 +237,24 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
         }
       }
 
-      // ---------------- particle-wall contacts (FP32 prefilter, FP64 geometry)
+      // ---------------- particle-wall contacts (FP32 prefilter, then out of line)
       const float xf[3] = {hx[0] + lx[0], hx[1] + lx[1], hx[2] + lx[2]};
       for (int k = 0; k < P.n_walls; k++) {
         if (!((wall_on >> k) & 1u)) continue;
         if (!wall_maybe_f(P.walls[k].kind, P.wf[k], xf, Rif, P.wall_margin)) continue;
-        const WallDev& Wl = P.walls[k];
-        double nrmd[3], dnd, ps[3];
-        if (!wall_geom_d(Wl, xi, (double)Rif, nrmd, &dnd, ps)) continue;
-        const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
-        double Vw[3];
-        cross3d(Wl.Om, arm, Vw);
-        for (int d = 0; d < 3; d++) Vw[d] += Wl.V[d];
-        const int bit = kMaxNbr + k;
-        double H[3] = {0.0, 0.0, 0.0};
-        if ((mold >> bit) & 1ull) {
-          const int ro = __popcll(mold & ((1ull << bit) - 1ull));
-          H[0] = Hold[ro * 3];
-          H[1] = Hold[ro * 3 + 1];
-          H[2] = Hold[ro * 3 + 2];
-        }
-        const float nf[3] = {(float)nrmd[0], (float)nrmd[1], (float)nrmd[2]};
-        const float dnf = (float)dnd;
-        float dv[3], dw[3];
+        const WallOut o = wall_contact_mixed(&P, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold, Hold, init);
+        if (!o.hit) continue;
         for (int d = 0; d < 3; d++) {
-          float h, l, s1, t1;
-          split_df(Vw[d], h, l);
-          df_diff(h, l, vh[d], vl[d], s1, t1);       // v_i - V_wall(p*)
-          dv[d] = s1 + t1;
-          split_df(Wl.Om[d], h, l);
-          df_diff(h, l, wh[d], wl[d], s1, t1);       // w_i - Omega
-          dw[d] = s1 + t1;
+          Ff[d] += o.F[d];
+          Mf[d] += o.M[d];
         }
-        const float rw[3] = {Rif * wif[0], Rif * wif[1], Rif * wif[2]};
-        const float vij[3] = {dv[0] + (rw[1] * nf[2] - rw[2] * nf[1]), dv[1] + (rw[2] * nf[0] - rw[0] * nf[2]),
-                              dv[2] + (rw[0] * nf[1] - rw[1] * nf[0])};
-        law_f(nf, dnf, vij, dw, Rif, mif, P.f_Ye_pw, P.f_Ge_pw, P.f_ceta_pw, P.f_mu_pw, P.f_mur_pw, P.rolling, dtf, H,
-              !init, Rif, Ff, Mf);
-        st.max_ovl = fmaxf(st.max_ovl, dnf / Rif);
+        st.max_ovl = fmaxf(st.max_ovl, o.ovl);
         st.wtouch++;
         if (rank < kHistStride) {
-          Hnew[rank * 3] = H[0];
-          Hnew[rank * 3 + 1] = H[1];
-          Hnew[rank * 3 + 2] = H[2];
-          mnew |= 1ull << bit;
+          Hnew[rank * 3] = o.H[0];
+          Hnew[rank * 3 + 1] = o.H[1];
+          Hnew[rank * 3 + 2] = o.H[2];
+          mnew |= 1ull << (kMaxNbr + k);
           rank++;
         } else {
           st.status |= kStCapacity;
@@ -245,41 +267,45 @@ __global__ void __launch_bounds__(kStepBlock, 7) k_step_mixed(Params P) {
       const float inv_I = 1.0f / (0.4f * mif * Rif * Rif);
       double xn[3], vn[3], wn[3];
       for (int d = 0; d < 3; d++) {
+        // the own FP64 state, read only now: fewer registers live through the contacts
+        const double xi = X[d * n + i], vi = V[d * n + i], wi = W[d * n + i];
         const double a = f2d_int(Ff[d] * inv_m + P.f_g[d]);
         const double al = f2d_int(Mf[d] * inv_I);
         if (init) {
-          vn[d] = fma(a, P.half_dt, vi[d]);
-          wn[d] = fma(al, P.half_dt, wi[d]);
+          vn[d] = fma(a, P.half_dt, vi);
+          wn[d] = fma(al, P.half_dt, wi);
         } else {
-          vn[d] = fma(a, P.dt, vi[d]);
-          wn[d] = fma(al, P.dt, wi[d]);
+          vn[d] = fma(a, P.dt, vi);
+          wn[d] = fma(al, P.dt, wi);
         }
         if (last) {
-          P.out_v[d * n + i] = init ? vi[d] : fma(a, P.half_dt, vi[d]);
-          P.out_w[d * n + i] = init ? wi[d] : fma(al, P.half_dt, wi[d]);
+          P.out_v[d * n + i] = init ? vi : fma(a, P.half_dt, vi);
+          P.out_w[d * n + i] = init ? wi : fma(al, P.half_dt, wi);
           P.out_F[d * n + i] = f2d_int(Ff[d]);
           P.out_M[d * n + i] = f2d_int(Mf[d]);
         }
-        xn[d] = fma(vn[d], P.dt, xi[d]);
+        xn[d] = fma(vn[d], P.dt, xi);
         P.x[nxt][d * n + i] = xn[d];
         P.v[nxt][d * n + i] = vn[d];
         P.w[nxt][d * n + i] = wn[d];
       }
-      P.shadow[nxt][i] = make_float4(hi_df(xn[0]), hi_df(xn[1]), hi_df(xn[2]), Rif);
       const bool alive = !below_sink(xn[2], P.z_sink_key);
       P.act[nxt][i] = alive ? 1 : 0;
+      float hn[3], ln[3];
+      for (int d = 0; d < 3; d++) split_df(xn[d], hn[d], ln[d]);
+      write_render(SHo + i, RDo + 3 * (size_t)i, hn, ln, vn, wn, Rif, alive);
       if (!(finite_d(xn[0]) && finite_d(xn[1]) && finite_d(xn[2]) && finite_d(vn[0]) && finite_d(vn[1]) &&
             finite_d(vn[2])))
         st.status |= kStNonfinite;
       if (alive) {
         st.active++;
-        // dynamic search trigger |x^{n+1} - x_ref|^2 > (skin/2)^2 without FP64 arithmetic
+        // dynamic search trigger |x^{n+1} - x_ref|^2 > (skin/2)^2 without FP64 arithmetic;
+        // x_ref is kept as its hi + lo pair
+        const float* xr = reinterpret_cast<const float*>(P.xref);
         float d2 = 0.f;
         for (int d = 0; d < 3; d++) {
-          float ah, al, bh, bl, s1, t1;
-          split_df(P.xref[d * n + i], ah, al);
-          split_df(xn[d], bh, bl);
-          df_diff(ah, al, bh, bl, s1, t1);
+          float s1, t1;
+          df_diff(xr[d * n + i], xr[(3 + d) * n + i], hn[d], ln[d], s1, t1);
           const float u = s1 + t1;
           d2 += u * u;
         }
