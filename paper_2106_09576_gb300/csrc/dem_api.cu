@@ -40,6 +40,7 @@ struct dem_ctx {
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kCellTileShift = 5;   // cell order: columns of 32 x 32 cells (cell_index)
 
 struct Layout {
   size_t total = 0;
@@ -661,6 +662,7 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
     P.inv_h[a] = (double)d.nc[a] / (cfg->domain_hi[a] - cfg->domain_lo[a]);
   }
   P.n_cells = d.n_cells;
+  P.cell_tile_shift = kCellTileShift;
   P.hcap_mask = (unsigned)(d.hcap - 1);
   P.dt = cfg->dt;
   P.half_dt = 0.5 * cfg->dt;

@@ -88,6 +88,7 @@ struct Params {
   int rolling;          // 0 none, 1 constant
   int rebuild_every;
   int nc[3];
+  int cell_tile_shift;   // cells are ordered in columns of 2^shift x 2^shift cells (cell_index)
   int n_cells;
   unsigned hcap_mask;   // hash capacity - 1 (power of two)
   double dt, half_dt;
@@ -155,6 +156,20 @@ __device__ __forceinline__ double sqdist_exact(double ax, double ay, double az, 
   s = dadd(s, dmul(dy, dy));
   s = dadd(s, dmul(dz, dz));
   return s;
+}
+
+// Position of cell (cx, cy, cz) in the sort order.  The grid is cut into columns of
+// T x T cells in x and y (T = 2^shift) spanning all of z; columns are taken in row-major
+// order, and inside a column x runs fastest, then y, then z.  A cell's 26 neighbours are
+// then within about T^2 cells of it, except across column faces, so the step kernel
+// finds most of a particle's neighbours still in L2 when it reads them.  With T at
+// least the grid's x and y extents this is the plain x-fastest order.
+__host__ __device__ __forceinline__ int cell_index(const int* nc, int shift, int cx, int cy, int cz) {
+  const int tile = 1 << shift;
+  const int tx = cx >> shift, ty = cy >> shift;
+  const int ix = cx - (tx << shift), iy = cy - (ty << shift);
+  const int wx = min(tile, nc[0] - (tx << shift)), hy = min(tile, nc[1] - (ty << shift));
+  return ((ty << shift) * nc[0] + (tx << shift) * hy) * nc[2] + (cz * hy + iy) * wx + ix;
 }
 
 // Error-free transformations in FP32 (Knuth two-sum, FMA two-product).

@@ -158,7 +158,7 @@ __global__ void k_cell_count(Params P) {
     int cx = cell_coord(X[p], P.lo[0], P.inv_h[0], P.nc[0]);
     int cy = cell_coord(X[n + p], P.lo[1], P.inv_h[1], P.nc[1]);
     int cz = cell_coord(X[2 * n + p], P.lo[2], P.inv_h[2], P.nc[2]);
-    key = (unsigned)((cz * P.nc[1] + cy) * P.nc[0] + cx);
+    key = (unsigned)cell_index(P.nc, P.cell_tile_shift, cx, cy, cz);
   } else {
     key = (unsigned)P.n_cells;  // bucket of particles that left the system
   }
@@ -273,7 +273,7 @@ __global__ void k_neighbors(Params P) {
       for (int dx = -1; dx <= 1; dx++) {
         const int x = cx + dx;
         if (x < 0 || x >= P.nc[0]) continue;
-        const int c = (z * P.nc[1] + y) * P.nc[0] + x;
+        const int c = cell_index(P.nc, P.cell_tile_shift, x, y, z);
         const int b = P.cell_start[c], e = P.cell_start[c + 1];
         for (int j = b; j < e; j++) {
           if (j == q) continue;
