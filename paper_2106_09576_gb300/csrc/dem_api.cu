@@ -132,7 +132,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
     o.mask[b] = L.add(n * 8);
     o.hist[b] = L.add(n * kHistStride * 3 * 8);
     const bool mixed = c->precision == DEM_PRECISION_MIXED;   // FP32 copies for neighbours
-    o.shadow[b] = L.add(mixed ? n * 16 : 0);
+    o.shadow[b] = L.add(n * 16);
     o.render[b] = L.add(mixed ? n * 48 : 0);
   }
   o.xref = L.add(3 * n * 8);

@@ -7,8 +7,11 @@
 //     rad[2], id[2]     FP32 / int32  reordered at each rebuild (parity ctl->sbuf)
 //     xref              FP64 [3][n]   positions at the last contact search; in a mixed
 //                                     context FP32 [6][n]: their hi parts, then lo parts
-//     shadow[2]         float4 [n]    {hx, hy, hz, R} of each particle (mixed path): what
-//                                     the contact prefilter reads; ping-pong with the state
+//     shadow[2]         float4 [n]    {hx, hy, hz, R} of each particle: written at each
+//                                     contact search (the FP32 filters of the fine search
+//                                     and the history restore read it) and, in a mixed
+//                                     context, by every step (the contact prefilter reads
+//                                     it); ping-pong with the state
 //     render[2]         float4 [n][3] {lx, ly, lz, in-system} {vx, vy, vz, wx}
 //                                     {wy, wz, 0, 0} (mixed path): what a contact partner
 //                                     reads; x = hx + lx to 2^-48; ping-pong with the state
@@ -157,6 +160,17 @@ __device__ __forceinline__ double sqdist_exact(double ax, double ay, double az, 
   s = dadd(s, dmul(dz, dz));
   return s;
 }
+
+// Bound on the error of an FP32 distance between two particles computed from the hi
+// parts of their positions (split_df truncates, |x - hi| < 2^-23 |x|): per axis the
+// difference of the hi parts is off by less than 2^-23 (a_i + a_j) plus its own rounding
+// (at most 2^-24 of a value below `reach`), so the distance is off by less than sqrt(3)
+// times that.  a_i, a_j are the largest coordinate magnitudes of the two particles.
+__device__ __forceinline__ float hi_distance_error(float a_i, float a_j, float reach) {
+  return 1.7320509f * (1.1920929e-7f * (a_i + a_j) * 1.0001f + 5.9604645e-8f * reach) + 1e-30f;
+}
+
+__device__ __forceinline__ float max_abs3(float4 h) { return fmaxf(fmaxf(fabsf(h.x), fabsf(h.y)), fabsf(h.z)); }
 
 // Position of cell (cx, cy, cz) in the sort order.  The grid is cut into columns of
 // T x T cells in x and y (T = 2^shift) spanning all of z; columns are taken in row-major

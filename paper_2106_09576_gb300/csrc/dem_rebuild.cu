@@ -208,17 +208,18 @@ __global__ void k_permute(Params P) {
   }
   const float r = P.rad[sb][p];
   const uint8_t a = P.act[cur][p];
+  float h[3], l[3];
+  for (int d = 0; d < 3; d++) split_df(xv[d], h[d], l[d]);
   if (P.precision == DEM_PRECISION_MIXED) {
-    float h[3], l[3];
     float* xr = reinterpret_cast<float*>(P.xref);
     for (int d = 0; d < 3; d++) {
-      split_df(xv[d], h[d], l[d]);
       xr[d * n + q] = h[d];
       xr[(3 + d) * n + q] = l[d];
     }
     write_render(P.shadow[nxt] + q, P.render[nxt] + 3 * (size_t)q, h, l, vv, wv, r, a != 0);
   } else {
     for (int d = 0; d < 3; d++) P.xref[d * n + q] = xv[d];
+    P.shadow[nxt][q] = make_float4(h[0], h[1], h[2], r);
   }
   P.act[nxt][q] = a;
   P.rad[sb ^ 1][q] = r;
@@ -239,10 +240,9 @@ __global__ void k_mirror_inactive(Params P) {
     P.w[cur][d * n + q] = P.w[nxt][d * n + q];
   }
   P.act[cur][q] = P.act[nxt][q];
-  if (P.precision == DEM_PRECISION_MIXED) {
-    P.shadow[cur][q] = P.shadow[nxt][q];
+  P.shadow[cur][q] = P.shadow[nxt][q];
+  if (P.precision == DEM_PRECISION_MIXED)
     for (int k = 0; k < 3; k++) P.render[cur][3 * (size_t)q + k] = P.render[nxt][3 * (size_t)q + k];
-  }
 }
 
 // ------------------------------------------------------------------ 4. fine search
@@ -256,8 +256,13 @@ __global__ void k_neighbors(Params P) {
   }
   const int nxt = P.ctl->cur ^ 1, sb1 = P.ctl->sbuf ^ 1;
   const double* X = P.x[nxt];
+  const float4* SH = P.shadow[nxt];
   const int* ids = P.id[sb1];
   const double xi = X[q], yi = X[n + q], zi = X[2 * n + q];
+  // FP32 decision from the hi parts where it is certain; the exact FP64 test otherwise
+  const float4 hi = SH[q];
+  const float ai = max_abs3(hi);
+  const float rcf = P.f_rc;
   const int cx = cell_coord(xi, P.lo[0], P.inv_h[0], P.nc[0]);
   const int cy = cell_coord(yi, P.lo[1], P.inv_h[1], P.nc[1]);
   const int cz = cell_coord(zi, P.lo[2], P.inv_h[2], P.nc[2]);
@@ -277,7 +282,16 @@ __global__ void k_neighbors(Params P) {
         const int b = P.cell_start[c], e = P.cell_start[c + 1];
         for (int j = b; j < e; j++) {
           if (j == q) continue;
-          if (sqdist_exact(xi, yi, zi, X[j], X[n + j], X[2 * n + j]) < P.rc2) {
+          const float4 hj = SH[j];
+          const float ex = hj.x - hi.x, ey = hj.y - hi.y, ez = hj.z - hi.z;
+          const float d2 = ex * ex + ey * ey + ez * ez;
+          const float err = hi_distance_error(ai, max_abs3(hj), 2.0f * rcf) + rcf * 1.2e-7f;
+          const float lo = fmaxf(rcf - err, 0.0f), up = rcf + err;
+          bool inside;
+          if (d2 < lo * lo * (1.0f - 1e-6f)) inside = true;
+          else if (d2 > up * up * (1.0f + 1e-6f)) inside = false;
+          else inside = sqdist_exact(xi, yi, zi, X[j], X[n + j], X[2 * n + j]) < P.rc2;
+          if (inside) {
             if (cnt < kMaxNbr) {
               // insertion by partner id keeps the list ordered as a serial pair loop
               const int idj = ids[j];
@@ -322,8 +336,20 @@ __global__ void k_hist_load(Params P) {
   double* H = P.hist[hn] + (size_t)q * kHistStride * 3;
   unsigned long long m = 0ull;
   int rank = 0;
+  // Only pairs that touch now can keep an overlap: the first force evaluation after this
+  // search drops the others.  The FP32 test below is widened by its error bound, so it
+  // never skips a touching pair.
+  const float4* SH = P.shadow[C->cur ^ 1];
+  const float4 hi = SH[q];
+  const float ai = max_abs3(hi);
   for (int k = 0; k < cnt; k++) {
-    const int b = ids[nb[k]];
+    const int j = nb[k];
+    const float4 hj = SH[j];
+    const float ex = hj.x - hi.x, ey = hj.y - hi.y, ez = hj.z - hi.z;
+    const float reach = hi.w + hj.w;
+    const float up = reach + hi_distance_error(ai, max_abs3(hj), 2.0f * reach);
+    if (ex * ex + ey * ey + ez * ez > up * up * (1.0f + 1e-6f)) continue;
+    const int b = ids[j];
     const unsigned long long key = pair_key(a, b);
     unsigned h = hash_slot(key, P.hcap_mask);
     for (unsigned probe = 0; probe <= P.hcap_mask; probe++) {
