@@ -653,6 +653,13 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   std::memset(&P, 0, sizeof(P));
   P.n = (int)cfg->n;
   P.precision = cfg->precision;
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 152;
+    P.sm_count = sms;
+  }
   P.rolling = cfg->rolling_model;
   P.rebuild_every = cfg->rebuild_every;
   for (int a = 0; a < 3; a++) {

@@ -88,6 +88,7 @@ struct Params {
   int n;
   int n_walls;
   int precision;        // 0 FP64, 1 mixed
+  int sm_count;         // SMs of the device the context runs on
   int rolling;          // 0 none, 1 constant
   int rebuild_every;
   int nc[3];
@@ -296,6 +297,15 @@ void scan_exclusive_i32(const int* in, int n, int* out, int* partials, cudaStrea
 void launch_step_fp64(const Params& P, cudaStream_t s);
 void launch_step_mixed(const Params& P, cudaStream_t s);
 
-constexpr int kStepBlock = 128;
+constexpr int kStepBlock = 128;   // largest block of the step kernels
+
+// Threads per block of a step kernel for n particles on sm_count SMs: 128 when the grid
+// covers every SM at least twice, smaller blocks for smaller systems so that their
+// particles spread over more SMs (the work per particle is long and latency-bound).
+inline int step_block(int n, int sm_count) {
+  if (n >= sm_count * 128 * 2) return 128;
+  if (n >= sm_count * 64 * 2) return 64;
+  return 32;
+}
 
 }  // namespace demgb

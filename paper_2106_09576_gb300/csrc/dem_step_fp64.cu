@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
 }
 
 void launch_step_fp64(const Params& P, cudaStream_t s) {
-  const int blocks = (P.n + kStepBlock - 1) / kStepBlock;
-  k_step_fp64<<<blocks, kStepBlock, 0, s>>>(P);
+  const int T = step_block(P.n, P.sm_count);
+  k_step_fp64<<<(P.n + T - 1) / T, T, 0, s>>>(P);
 }
 
 }  // namespace demgb

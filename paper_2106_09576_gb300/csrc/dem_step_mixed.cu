@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
 }
 
 void launch_step_mixed(const Params& P, cudaStream_t s) {
-  const int blocks = (P.n + kStepBlock - 1) / kStepBlock;
-  k_step_mixed<<<blocks, kStepBlock, 0, s>>>(P);
+  const int T = step_block(P.n, P.sm_count);
+  k_step_mixed<<<(P.n + T - 1) / T, T, 0, s>>>(P);
 }
 
 }  // namespace demgb

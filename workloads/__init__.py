@@ -222,13 +222,14 @@ def drum(n: int = 200_000, seed: int | None = None, rmin: float = 1.5e-3, rmax: 
 
 def silo(n: int = 4_300_000, seed: int | None = None, d: float = 5e-3, R: float = 0.5,
          orifice: float = 0.05, height: float = 1.0, t_open: float = 1e300,
-         precision: str = "mixed", spacing: float = 1.1, jitter: float = 0.025) -> Workload:
+         precision: str = "mixed", spacing: float = 1.1, jitter: float = 0.025,
+         z_sink: float = -0.1) -> Workload:
     """Flat-bottomed cylindrical silo: cylinder wall, annular bottom with a central
     orifice, a floating plug over the orifice until t_open; simple cubic fill at
     `spacing` d with jitter <= `jitter` d (1.1 and 0.025: a loose fill that falls and
     packs; 0.995 and 0.002: a packed bed in which every sphere touches its lattice
     neighbours).  Search with a skin of 0.5 d (r_c = 1.5 d), rebuilt when a displacement
-    exceeds 0.25 d; particles are removed 0.1 m below the orifice."""
+    exceeds 0.25 d; particles are removed below z_sink (default 0.1 m below the orifice)."""
     rng = np.random.Generator(np.random.PCG64(seed_for(3) if seed is None else seed))
     r = 0.5 * d
     a = spacing * d
@@ -251,8 +252,8 @@ def silo(n: int = 4_300_000, seed: int | None = None, d: float = 5e-3, R: float 
              annulus((0, 0, 0), (0, 0, 1), R, orifice),
              plane((0, 0, 0), (0, 0, 1), t_off=t_open)]
     mat = material(mu_slide=0.5, mu_roll=0.1)
-    cfg = _base_cfg(domain_lo=(-R, -R, -0.1 - d), domain_hi=(R, R, top), dt=1e-5,
-                    particle=mat, wall=dict(mat), skin=0.5 * d, z_sink=-0.1,
+    cfg = _base_cfg(domain_lo=(-R, -R, z_sink - d), domain_hi=(R, R, top), dt=1e-5,
+                    particle=mat, wall=dict(mat), skin=0.5 * d, z_sink=z_sink,
                     precision=precision)
     return Workload("silo", cfg, walls, x, np.zeros((n, 3)), np.zeros((n, 3)),
                     np.full(n, r, dtype=np.float32))
