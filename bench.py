@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-batched", action="store_true", help="skip the batch of 512 drums")
+    p.add_argument("--batched-steps", type=int, default=10000)
     return p.parse_args()
 
 
@@ -263,6 +265,68 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def run_batched(args, dev, world):
+    """512 drums (particle counts log-uniform in 500-20,000) in one batch context, launch
+    parameters picked by the autotuner, timed over --batched-steps steps from the seeded
+    fill; beside it, the same drums run one system per context, timed on 16 of them spread
+    over the size range and extrapolated to all 512 by particle count."""
+    import torch
+    import workloads
+    from paper_2106_09576_gb300 import DEM
+    from paper_2106_09576_gb300.autotune import autotune
+
+    b = workloads.batched_drums(precision="mixed")
+    over, table = autotune(b, device=dev)
+    cfg = dict(b.cfg, **over)
+    g = DEM(cfg, b.x, b.v, b.w, b.radius, b.walls, precision="mixed", device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    g.step(args.batched_steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    st = g.stats()
+    value = sum_over_ranks(b.n * args.batched_steps, world) / (ms / 1e3)
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    # plain: one context per drum, on a sample spread over the size range
+    insts = b.cfg["instances"]
+    order = sorted(range(len(insts)), key=lambda k: insts[k]["n"])
+    sample = [order[int(round(q * (len(order) - 1)))] for q in np.linspace(0.0, 1.0, 16)]
+    k_steps = min(1000, args.batched_steps)
+    rates = []
+    for k in sample:
+        wk = workloads.instance_workload(b, k)
+        gk = DEM(wk.cfg, wk.x, wk.v, wk.w, wk.radius, wk.walls, precision="mixed", device=dev)
+        gk.step(10)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        gk.step(k_steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        rates.append((wk.n, wk.n * k_steps / (e0.elapsed_time(e1) / 1e3)))
+        gk.close()
+    ns = np.array([r[0] for r in rates], float)
+    rs = np.array([r[1] for r in rates], float)
+    all_n = np.array([I["n"] for I in insts], float)
+    est_rate = np.exp(np.interp(np.log(all_n), np.log(ns), np.log(rs)))
+    plain_seconds = float(np.sum(all_n * args.batched_steps / est_rate))
+    plain_value = float(all_n.sum() * args.batched_steps / plain_seconds)
+    return {"workload": f"batched-drums-512 ({b.n} spheres, N log-uniform in 500-20000, r in 1-3 mm)",
+            "n": b.n, "instances": len(insts), "steps": args.batched_steps, "value": value, "unit": UNIT,
+            "ms_per_step": ms / args.batched_steps, "dt": b.cfg["dt"], "precision": "mixed",
+            "autotune": {"chosen": over, "candidates": table},
+            "rebuilds": st["rebuilds"], "n_touch_last_step": st["n_touch"],
+            "plain": {"value": plain_value, "unit": UNIT, "method": "one context per drum, 16 drums timed over "
+                      f"{k_steps} steps each, extrapolated to all 512 by particle count"},
+            "speedup_vs_plain": value / plain_value,
+            "state_vs_plain": "bit-identical per instance (tests/test_gpu_batch.py)"}
+
+
 def run_ours(args):
     import torch
     from paper_2106_09576_gb300 import DEM
@@ -369,6 +433,10 @@ def run_ours(args):
         gf.close()
         del gf
         torch.cuda.empty_cache()
+
+    # ---------------- batch of 512 independent drums in one context (one launch per step)
+    if not args.no_batched:
+        extra["batched"] = run_batched(args, dev, world)
 
     # ---------------- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None

@@ -82,11 +82,15 @@ typedef struct {
                                 some |x - x_ref| > skin/2 (Sec. 3.1) */
   int32_t precision;         /* DEM_PRECISION_FP64 or DEM_PRECISION_MIXED */
   int32_t rolling_model;     /* 0 none, 1 constant torque model (Table rolling_torque) */
-  int32_t reserved0;
+  int32_t n_instances;       /* 0 or 1: one system.  > 1: a batch of independent systems in
+                                one context (dem_set_instances); no counterpart in the paper */
   double domain_lo[3];       /* box of the cell grid; particles outside are clamped to */
   double domain_hi[3];       /* the border cells (correct, but slower if many) */
   double z_sink;             /* a particle whose centre drops below z_sink leaves the system */
   double max_overlap_ratio;  /* > 0: DEM_ERR_OVERLAP when delta_n > ratio * R_min; 0 = off */
+  int32_t step_block;        /* threads per block of the step kernel: 32, 64 or 128; 0 = chosen
+                                from n and the SM count (a launch parameter, not physics) */
+  int32_t reserved1;
 } dem_config;
 
 /* Analytic wall (the paper meshes the boundary; see Sec. 2.1 last paragraph and
@@ -111,6 +115,24 @@ typedef struct {
   double omega, rot_origin[3], rot_axis[3], velocity[3];
   double t_on, t_off;
 } dem_wall;
+
+#define DEM_MAX_INSTANCE_WALLS 4
+
+/* One member of a batch (dem_config.n_instances > 1).  The paper simulates one system at
+ * a time; a batch runs many independent systems -- each with its own particles, materials
+ * and walls -- through the same kernels, one step of all of them per launch.  Instance k
+ * owns the particles first[k] <= i < first[k+1] (caller order; first[n_instances] = n).
+ * Particles of different instances never interact, even where their regions overlap;
+ * placing instances in disjoint regions of the domain keeps the cells sparse.  The
+ * top-level dem_config materials and dem_set_walls are not used by a batch. */
+typedef struct {
+  int64_t first;              /* first particle of the instance, caller order, increasing */
+  dem_material particle;      /* particle-particle contacts */
+  dem_material wall;          /* particle-wall contacts (mixing as for a single system) */
+  int32_t n_walls;            /* <= DEM_MAX_INSTANCE_WALLS */
+  int32_t reserved0;
+  dem_wall walls[DEM_MAX_INSTANCE_WALLS];
+} dem_instance;
 
 typedef struct {
   int64_t steps;              /* time steps taken since the state was set */
@@ -142,6 +164,15 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
 /* Replaces the walls (host array, copied; n_walls <= DEM_MAX_WALLS) and clears the
  * particle-wall tangential overlaps.  Forces are re-evaluated before the next step. */
 dem_status dem_set_walls(dem_ctx* ctx, const dem_wall* walls, int32_t n_walls);
+
+/* Batch contexts only (cfg.n_instances > 1): gives each instance its particle range,
+ * materials and walls (host array of cfg.n_instances entries, copied).  Must be called
+ * before the first dem_step; calling it again replaces the tables, clears the particle-
+ * wall tangential overlaps and re-evaluates forces before the next step.  DEM_ERR_ARG if
+ * the ranges are not increasing from 0, a wall count exceeds DEM_MAX_INSTANCE_WALLS or a
+ * material is invalid; DEM_ERR_STATE on a context that is not a batch.  No counterpart
+ * in the paper (it runs one system per process group). */
+dem_status dem_set_instances(dem_ctx* ctx, const dem_instance* instances, int32_t n_instances);
 
 /* Advances n_steps >= 0 time steps, asynchronously on the context's stream.  Returns
  * DEM_ERR_STATE if a sticky device error is already known on the host. */

@@ -34,6 +34,7 @@ struct dem_ctx {
   int n_walls = 0;
   cudaGraphExec_t exec = nullptr;
   bool eager = false;
+  bool instances_set = false;  // batch contexts: dem_set_instances has been called
   unsigned sticky = 0;     // device status bits already reported on the host
 };
 
@@ -60,17 +61,28 @@ struct Derived {
 
 bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
+bool valid_material(const dem_material& m) {
+  return m.young > 0.0 && m.poisson > -1.0 && m.poisson < 0.5 && m.restitution > 0.0 && m.restitution <= 1.0 &&
+         m.mu_slide >= 0.0 && m.mu_roll >= 0.0;
+}
+
+bool valid_wall(const dem_wall& W) {
+  if (W.kind < 0 || W.kind > 2) return false;
+  const double nn = std::sqrt(W.normal[0] * W.normal[0] + W.normal[1] * W.normal[1] + W.normal[2] * W.normal[2]);
+  if (!(nn > 0.0)) return false;
+  if (W.kind >= 1 && !(W.radius > 0.0)) return false;
+  if (W.kind == 2 && !(W.inner_radius >= 0.0 && W.inner_radius < W.radius)) return false;
+  return true;
+}
+
 dem_status derive(const dem_config* c, Derived* d) {
   if (!c || c->n <= 0 || c->n >= (1LL << 31) - 64) return DEM_ERR_ARG;
   if (!(c->density > 0.0) || !(c->radius_max > 0.0) || !(c->dt > 0.0)) return DEM_ERR_ARG;
   if (c->precision != DEM_PRECISION_FP64 && c->precision != DEM_PRECISION_MIXED) return DEM_ERR_ARG;
   if (c->rolling_model != 0 && c->rolling_model != 1) return DEM_ERR_ARG;
-  const dem_material* m[2] = {&c->particle, &c->wall};
-  for (auto* mm : m) {
-    if (!(mm->young > 0.0) || !(mm->poisson > -1.0 && mm->poisson < 0.5)) return DEM_ERR_ARG;
-    if (!(mm->restitution > 0.0 && mm->restitution <= 1.0)) return DEM_ERR_ARG;
-    if (!(mm->mu_slide >= 0.0) || !(mm->mu_roll >= 0.0)) return DEM_ERR_ARG;
-  }
+  if (c->n_instances < 0 || c->n_instances > c->n) return DEM_ERR_ARG;
+  if (c->step_block != 0 && c->step_block != 32 && c->step_block != 64 && c->step_block != 128) return DEM_ERR_ARG;
+  if (!valid_material(c->particle) || !valid_material(c->wall)) return DEM_ERR_ARG;
   if (!finite3(c->gravity) || !finite3(c->domain_lo) || !finite3(c->domain_hi)) return DEM_ERR_ARG;
   // search threshold: r_c = d_max + skin, or factor * d_max (Sec. 3.2), same arithmetic
   // as the CPU statement of the method
@@ -111,7 +123,7 @@ dem_status derive(const dem_config* c, Derived* d) {
 }
 
 struct Offsets {
-  size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], xref, nbr, nbr_cnt, key, local, order,
+  size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], inst[2], itab, xref, nbr, nbr_cnt, key, local, order,
       cell_count, cell_start, scan_tmp, hkey, hval, wall_tmp, wall_tmp_mask, out_v, out_w, out_F, out_M,
       stage, ctl, io_cnt, io_off;
   size_t total;
@@ -135,6 +147,9 @@ Offsets layout(const dem_config* c, const Derived& d) {
     o.shadow[b] = L.add(n * 16);
     o.render[b] = L.add(mixed ? n * 48 : 0);
   }
+  const size_t n_inst = c->n_instances > 1 ? (size_t)c->n_instances : 0;
+  for (int b = 0; b < 2; b++) o.inst[b] = L.add(n_inst ? n * 4 : 0);
+  o.itab = L.add(n_inst * sizeof(InstDev));
   o.xref = L.add(3 * n * 8);
   o.nbr = L.add(n * kMaxNbr * 4);
   o.nbr_cnt = L.add(n * 4);
@@ -212,6 +227,14 @@ __global__ void k_in_act(Params P, const uint8_t* src) {
   if (p >= P.n) return;
   const Control* C = P.ctl;
   P.act[C->cur][p] = src[P.id[C->sbuf][p]] ? 1 : 0;
+}
+
+// caller order (stage) -> instance of each sorted particle, gathered through id
+__global__ void k_in_inst(Params P, const int* src) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.n) return;
+  const int sb = P.ctl->sbuf;
+  P.inst[sb][p] = src[P.id[sb][p]];
 }
 
 __global__ void k_init_identity(Params P) {
@@ -422,34 +445,62 @@ double eta_coeff(double e) {
   return -2.0 * std::sqrt(5.0 / 6.0) * beta;
 }
 
+void fill_materials(const dem_material& part, const dem_material& wall, MatD* md, MatF* mf) {
+  md->Ye_pp = eff_young(part, part);
+  md->Ge_pp = eff_shear(part, part);
+  md->ceta_pp = eta_coeff(part.restitution);
+  md->mu_pp = part.mu_slide;
+  md->mur_pp = part.mu_roll;
+  md->Ye_pw = eff_young(part, wall);
+  md->Ge_pw = eff_shear(part, wall);
+  md->ceta_pw = eta_coeff(wall.restitution);
+  md->mu_pw = wall.mu_slide;
+  md->mur_pw = wall.mu_roll;
+  mf->Ye_pp = (float)md->Ye_pp;
+  mf->Ge_pp = (float)md->Ge_pp;
+  mf->ceta_pp = (float)md->ceta_pp;
+  mf->mu_pp = (float)md->mu_pp;
+  mf->mur_pp = (float)md->mur_pp;
+  mf->Ye_pw = (float)md->Ye_pw;
+  mf->Ge_pw = (float)md->Ge_pw;
+  mf->ceta_pw = (float)md->ceta_pw;
+  mf->mu_pw = (float)md->mu_pw;
+  mf->mur_pw = (float)md->mur_pw;
+}
+
+void to_device_wall(const dem_wall& s, WallDev* W, WallF* F) {
+  std::memset(W, 0, sizeof(*W));
+  std::memset(F, 0, sizeof(*F));
+  W->kind = s.kind;
+  double nn = std::sqrt(s.normal[0] * s.normal[0] + s.normal[1] * s.normal[1] + s.normal[2] * s.normal[2]);
+  double na = std::sqrt(s.rot_axis[0] * s.rot_axis[0] + s.rot_axis[1] * s.rot_axis[1] + s.rot_axis[2] * s.rot_axis[2]);
+  for (int d = 0; d < 3; d++) {
+    W->p[d] = s.point[d];
+    W->n[d] = s.normal[d] / nn;
+    W->Om[d] = na > 0.0 ? s.omega * s.rot_axis[d] / na : 0.0;
+    W->c[d] = s.rot_origin[d];
+    W->V[d] = s.velocity[d];
+  }
+  W->radius = s.radius;
+  W->inner = s.inner_radius;
+  W->t_on = s.t_on;
+  W->t_off = s.t_off;
+  for (int d = 0; d < 3; d++) {
+    F->p[d] = (float)W->p[d];
+    F->n[d] = (float)W->n[d];
+  }
+  F->radius = (float)W->radius;
+  F->inner = (float)W->inner;
+}
+
 void fill_walls(dem_ctx* c) {
   for (int k = 0; k < kMaxWalls; k++) {
-    WallDev& W = c->P.walls[k];
-    std::memset(&W, 0, sizeof(W));
-    if (k >= c->n_walls) continue;
-    const dem_wall& s = c->walls[k];
-    W.kind = s.kind;
-    double nn = std::sqrt(s.normal[0] * s.normal[0] + s.normal[1] * s.normal[1] + s.normal[2] * s.normal[2]);
-    double na =
-        std::sqrt(s.rot_axis[0] * s.rot_axis[0] + s.rot_axis[1] * s.rot_axis[1] + s.rot_axis[2] * s.rot_axis[2]);
-    for (int d = 0; d < 3; d++) {
-      W.p[d] = s.point[d];
-      W.n[d] = s.normal[d] / nn;
-      W.Om[d] = na > 0.0 ? s.omega * s.rot_axis[d] / na : 0.0;
-      W.c[d] = s.rot_origin[d];
-      W.V[d] = s.velocity[d];
+    if (k < c->n_walls) {
+      to_device_wall(c->walls[k], &c->P.walls[k], &c->P.wf[k]);
+    } else {
+      std::memset(&c->P.walls[k], 0, sizeof(WallDev));
+      std::memset(&c->P.wf[k], 0, sizeof(WallF));
     }
-    W.radius = s.radius;
-    W.inner = s.inner_radius;
-    W.t_on = s.t_on;
-    W.t_off = s.t_off;
-    WallF& F = c->P.wf[k];
-    for (int d = 0; d < 3; d++) {
-      F.p[d] = (float)W.p[d];
-      F.n[d] = (float)W.n[d];
-    }
-    F.radius = (float)W.radius;
-    F.inner = (float)W.inner;
   }
   c->P.n_walls = c->n_walls;
 }
@@ -687,31 +738,14 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
       ext = std::max(ext, std::max(std::fabs(cfg->domain_lo[a]), std::fabs(cfg->domain_hi[a])));
     P.wall_margin = (float)(1e-6 * std::max(1.0, ext) + 1e-9);
   }
-  P.Ye_pp = eff_young(cfg->particle, cfg->particle);
-  P.Ge_pp = eff_shear(cfg->particle, cfg->particle);
-  P.ceta_pp = eta_coeff(cfg->particle.restitution);
-  P.mu_pp = cfg->particle.mu_slide;
-  P.mur_pp = cfg->particle.mu_roll;
-  P.Ye_pw = eff_young(cfg->particle, cfg->wall);
-  P.Ge_pw = eff_shear(cfg->particle, cfg->wall);
-  P.ceta_pw = eta_coeff(cfg->wall.restitution);
-  P.mu_pw = cfg->wall.mu_slide;
-  P.mur_pw = cfg->wall.mu_roll;
+  fill_materials(cfg->particle, cfg->wall, &P.md, &P.mf);
   P.f_density = (float)P.density;
   P.f_dt = (float)P.dt;
   for (int a = 0; a < 3; a++) P.f_g[a] = (float)P.g[a];
   P.f_disp_lim2 = (float)(P.disp_lim2 * (1.0 - 1e-5));   // conservative: rebuild slightly early
   P.f_rc = (float)d.rc;
-  P.f_Ye_pp = (float)P.Ye_pp;
-  P.f_Ge_pp = (float)P.Ge_pp;
-  P.f_ceta_pp = (float)P.ceta_pp;
-  P.f_mu_pp = (float)P.mu_pp;
-  P.f_mur_pp = (float)P.mur_pp;
-  P.f_Ye_pw = (float)P.Ye_pw;
-  P.f_Ge_pw = (float)P.Ge_pw;
-  P.f_ceta_pw = (float)P.ceta_pw;
-  P.f_mu_pw = (float)P.mu_pw;
-  P.f_mur_pw = (float)P.mur_pw;
+  P.step_block = cfg->step_block;
+  P.n_inst = cfg->n_instances > 1 ? cfg->n_instances : 0;
   {
     long long zb;
     double zs = cfg->z_sink;
@@ -729,7 +763,9 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
     P.hist[b] = (double*)(base + o.hist[b]);
     P.shadow[b] = (float4*)(base + o.shadow[b]);
     P.render[b] = (float4*)(base + o.render[b]);
+    P.inst[b] = (int*)(base + o.inst[b]);
   }
+  P.itab = (const InstDev*)(base + o.itab);
   P.xref = (double*)(base + o.xref);
   P.nbr = (int*)(base + o.nbr);
   P.nbr_cnt = (int*)(base + o.nbr_cnt);
@@ -786,14 +822,9 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
 
 dem_status dem_set_walls(dem_ctx* c, const dem_wall* walls, int32_t n_walls) {
   if (!c || n_walls < 0 || n_walls > kMaxWalls || (n_walls > 0 && !walls)) return DEM_ERR_ARG;
-  for (int k = 0; k < n_walls; k++) {
-    const dem_wall& W = walls[k];
-    if (W.kind < 0 || W.kind > 2) return DEM_ERR_ARG;
-    double nn = std::sqrt(W.normal[0] * W.normal[0] + W.normal[1] * W.normal[1] + W.normal[2] * W.normal[2]);
-    if (!(nn > 0.0)) return DEM_ERR_ARG;
-    if (W.kind >= 1 && !(W.radius > 0.0)) return DEM_ERR_ARG;
-    if (W.kind == 2 && !(W.inner_radius >= 0.0 && W.inner_radius < W.radius)) return DEM_ERR_ARG;
-  }
+  if (c->P.n_inst > 1) return DEM_ERR_STATE;   // a batch takes its walls per instance
+  for (int k = 0; k < n_walls; k++)
+    if (!valid_wall(walls[k])) return DEM_ERR_ARG;
   for (int k = 0; k < n_walls; k++) c->walls[k] = walls[k];
   c->n_walls = n_walls;
   fill_walls(c);
@@ -804,15 +835,55 @@ dem_status dem_set_walls(dem_ctx* c, const dem_wall* walls, int32_t n_walls) {
   return cuda_status(cudaGetLastError());
 }
 
+dem_status dem_set_instances(dem_ctx* c, const dem_instance* inst, int32_t n_instances) {
+  if (!c || !inst) return DEM_ERR_ARG;
+  if (c->P.n_inst <= 1) return DEM_ERR_STATE;
+  if (n_instances != c->P.n_inst) return DEM_ERR_ARG;
+  const long long n = c->P.n;
+  std::vector<InstDev> tab((size_t)n_instances);
+  std::vector<int> of((size_t)n);
+  for (int k = 0; k < n_instances; k++) {
+    const dem_instance& I = inst[k];
+    const long long lo = I.first, hi = k + 1 < n_instances ? inst[k + 1].first : n;
+    if (lo < 0 || hi > n || lo > hi || (k == 0 && lo != 0)) return DEM_ERR_ARG;
+    if (!valid_material(I.particle) || !valid_material(I.wall)) return DEM_ERR_ARG;
+    if (I.n_walls < 0 || I.n_walls > kMaxInstWalls) return DEM_ERR_ARG;
+    InstDev& D = tab[(size_t)k];
+    std::memset(&D, 0, sizeof(D));
+    fill_materials(I.particle, I.wall, &D.md, &D.mf);
+    D.n_walls = I.n_walls;
+    for (int w = 0; w < I.n_walls; w++) {
+      if (!valid_wall(I.walls[w])) return DEM_ERR_ARG;
+      to_device_wall(I.walls[w], &D.walls[w], &D.wf[w]);
+    }
+    for (long long i = lo; i < hi; i++) of[(size_t)i] = k;
+  }
+  // the instance of each particle, gathered into the current sorted order through id
+  if (n * 4 > (long long)c->stage_bytes) return DEM_ERR_CAPACITY;
+  CK(cudaMemcpyAsync((void*)c->P.itab, tab.data(), tab.size() * sizeof(InstDev), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->P.stage, of.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+  const int T = 256;
+  k_in_inst<<<blocks_for(n, T), T, 0, c->stream>>>(c->P, (const int*)c->P.stage);
+  k_clear_wall_bits<<<blocks_for(n, T), T, 0, c->stream>>>(c->P);
+  k_mark<<<1, 1, 0, c->stream>>>(c->P.ctl, 1, -1, 0);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));   // the host tables above go out of scope
+  destroy_graph(c);
+  c->instances_set = true;
+  return DEM_OK;
+}
+
 dem_status dem_step(dem_ctx* c, int64_t n_steps) {
   if (!c || n_steps < 0) return DEM_ERR_ARG;
   if (c->sticky) return DEM_ERR_STATE;
+  if (c->P.n_inst > 1 && !c->instances_set) return DEM_ERR_STATE;
   if (n_steps == 0) return DEM_OK;
   return run_iterations(c, n_steps);
 }
 
 dem_status dem_step_profiled(dem_ctx* c, int64_t n_steps, double* step_kernel_ms, double* search_ms,
                              int64_t* step_launches, int64_t* searches) {
+  if (c && c->P.n_inst > 1 && !c->instances_set) return DEM_ERR_STATE;
   if (!c || n_steps < 0) return DEM_ERR_ARG;
   if (c->sticky) return DEM_ERR_STATE;
   double ks = 0.0, ss = 0.0;

@@ -56,6 +56,29 @@ struct WallF {
   float p[3], n[3], radius, inner;
 };
 
+// Material constants of one contact type pair (Table equation_parameters): effective Y
+// and G, -2 sqrt(5/6) beta, sliding and rolling friction; particle-particle (_pp) and
+// particle-wall (_pw).  MatF holds their FP32 copies for the mixed path.
+struct MatD {
+  double Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp;
+  double Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
+};
+struct MatF {
+  float Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp;
+  float Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
+};
+
+// One member of a batch: its materials and walls (device table indexed by instance).
+constexpr int kMaxInstWalls = 4;
+struct InstDev {
+  MatD md;
+  MatF mf;
+  int n_walls;
+  int pad;
+  WallDev walls[kMaxInstWalls];
+  WallF wf[kMaxInstWalls];
+};
+
 // Device-resident control block: everything that changes from step to step.
 struct Control {
   int cur;              // state parity holding the positions of the next force evaluation
@@ -89,6 +112,7 @@ struct Params {
   int n_walls;
   int precision;        // 0 FP64, 1 mixed
   int sm_count;         // SMs of the device the context runs on
+  int step_block;       // threads per step-kernel block; 0 = step_block(n, sm_count)
   int rolling;          // 0 none, 1 constant
   int rebuild_every;
   int nc[3];
@@ -104,16 +128,17 @@ struct Params {
   double max_overlap_ratio;
   double lo[3], inv_h[3];
   float wall_margin;    // FP32 prefilter margin for walls (m)
-  // material constants (Table equation_parameters): effective Y and G, -2 sqrt(5/6) beta
-  double Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp;
-  double Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
+  MatD md;              // material constants of a single system
   WallDev walls[kMaxWalls];
   // FP32 copies of uniform constants (mixed path), computed once on the host
   float f_density, f_dt, f_g[3], f_disp_lim2, f_rc;
-  float f_Ye_pp, f_Ge_pp, f_ceta_pp, f_mu_pp, f_mur_pp;
-  float f_Ye_pw, f_Ge_pw, f_ceta_pw, f_mu_pw, f_mur_pw;
+  MatF mf;
   long long z_sink_key;   // ordered-integer image of z_sink (exact comparison without FP64)
   WallF wf[kMaxWalls];
+  // batch (n_inst > 1): per-instance materials and walls replace md, mf, walls, wf
+  int n_inst;
+  const InstDev* itab;  // [n_inst]
+  int* inst[2];         // [n] instance of each particle, reordered with rad/id (parity sbuf)
   // buffers
   double* x[2];
   double* v[2];

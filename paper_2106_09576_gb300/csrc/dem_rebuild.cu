@@ -224,6 +224,7 @@ __global__ void k_permute(Params P) {
   P.act[nxt][q] = a;
   P.rad[sb ^ 1][q] = r;
   P.id[sb ^ 1][q] = P.id[sb][p];
+  if (P.n_inst > 1) P.inst[sb ^ 1][q] = P.inst[sb][p];
 }
 
 // Particles out of the system sit after the active ones and are never touched by the
@@ -263,6 +264,9 @@ __global__ void k_neighbors(Params P) {
   const float4 hi = SH[q];
   const float ai = max_abs3(hi);
   const float rcf = P.f_rc;
+  // in a batch, particles of different instances never interact
+  const int* inst = P.n_inst > 1 ? P.inst[sb1] : nullptr;
+  const int my_inst = inst ? inst[q] : 0;
   const int cx = cell_coord(xi, P.lo[0], P.inv_h[0], P.nc[0]);
   const int cy = cell_coord(yi, P.lo[1], P.inv_h[1], P.nc[1]);
   const int cz = cell_coord(zi, P.lo[2], P.inv_h[2], P.nc[2]);
@@ -282,6 +286,7 @@ __global__ void k_neighbors(Params P) {
         const int b = P.cell_start[c], e = P.cell_start[c + 1];
         for (int j = b; j < e; j++) {
           if (j == q) continue;
+          if (inst && inst[j] != my_inst) continue;
           const float4 hj = SH[j];
           const float ex = hj.x - hi.x, ey = hj.y - hi.y, ez = hj.z - hi.z;
           const float d2 = ex * ex + ey * ey + ez * ez;

@@ -11,7 +11,8 @@
 
 namespace demgb {
 
-__global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
+template <bool kBatch>
+__global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant__ Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, sb = C->sbuf, hc = C->hc;
   const bool init = C->init != 0, last = C->last != 0;
@@ -62,6 +63,18 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
       const int cnt = P.nbr_cnt[i];
       unsigned long long mnew = 0ull;
       int rank = 0;
+      // materials and walls: the context's, or those of the particle's instance in a batch
+      const InstDev* I = kBatch ? P.itab + P.inst[sb][i] : nullptr;
+      const MatD& Mt = kBatch ? I->md : P.md;
+      const WallDev* WLs = kBatch ? I->walls : P.walls;
+      const int n_walls = kBatch ? I->n_walls : P.n_walls;
+      unsigned won = wall_on;
+      if (kBatch) {
+        won = 0u;
+        const double t = (double)C->step * P.dt;
+        for (int k = 0; k < n_walls; k++)
+          if (t >= WLs[k].t_on && t < WLs[k].t_off) won |= 1u << k;
+      }
       const double Ri = (double)RAD[i];
       const double mi = P.density * (4.0 / 3.0) * 3.14159265358979323846 * Ri * Ri * Ri;
       const double Ii = 0.4 * mi * Ri * Ri;
@@ -98,7 +111,7 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
           H[2] = Hold[ro * 3 + 2];
         }
         double f[3], nxFt[3], Mr[3];
-        law_d(nrm, dn, vij, dw, Re, me, P.Ye_pp, P.Ge_pp, P.ceta_pp, P.mu_pp, P.mur_pp, P.rolling, P.dt, H, !init,
+        law_d(nrm, dn, vij, dw, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp, P.rolling, P.dt, H, !init,
               f, nxFt, Mr);
         for (int d = 0; d < 3; d++) {
           F[d] += f[d];
@@ -118,9 +131,9 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
       }
 
       // particle-wall contacts (Sec. 2.1 last paragraph; walls move per Sec. 3.6)
-      for (int k = 0; k < P.n_walls; k++) {
-        if (!((wall_on >> k) & 1u)) continue;
-        const WallDev& Wl = P.walls[k];
+      for (int k = 0; k < n_walls; k++) {
+        if (!((won >> k) & 1u)) continue;
+        const WallDev& Wl = WLs[k];
         double nrm[3], dn, ps[3];
         if (!wall_geom_d(Wl, xi, Ri, nrm, &dn, ps)) continue;
         const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
           dw[d] = wi[d] - Wl.Om[d];
         }
         double f[3], nxFt[3], Mr[3];
-        law_d(nrm, dn, vij, dw, Ri, mi, P.Ye_pw, P.Ge_pw, P.ceta_pw, P.mu_pw, P.mur_pw, P.rolling, P.dt, H, !init, f,
+        law_d(nrm, dn, vij, dw, Ri, mi, Mt.Ye_pw, Mt.Ge_pw, Mt.ceta_pw, Mt.mu_pw, Mt.mur_pw, P.rolling, P.dt, H, !init, f,
               nxFt, Mr);
         for (int d = 0; d < 3; d++) {
           F[d] += f[d];
@@ -206,8 +219,11 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(Params P) {
 }
 
 void launch_step_fp64(const Params& P, cudaStream_t s) {
-  const int T = step_block(P.n, P.sm_count);
-  k_step_fp64<<<(P.n + T - 1) / T, T, 0, s>>>(P);
+  const int T = P.step_block > 0 ? P.step_block : step_block(P.n, P.sm_count);
+  if (P.n_inst > 1)
+    k_step_fp64<true><<<(P.n + T - 1) / T, T, 0, s>>>(P);
+  else
+    k_step_fp64<false><<<(P.n + T - 1) / T, T, 0, s>>>(P);
 }
 
 }  // namespace demgb

@@ -28,13 +28,15 @@ struct WallOut {
   int hit;
 };
 
-__device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, int k, int i, int cur, double x0, double x1,
-                                                   double x2, float Rif, float mif, unsigned long long mold,
-                                                   const double* Hold, bool init) {
+template <bool kBatch>
+__device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstDev* I, int k, int i, int cur, double x0,
+                                                   double x1, double x2, float Rif, float mif,
+                                                   unsigned long long mold, const double* Hold, bool init) {
   const Params& P = *Pp;
+  const WallDev& Wl = kBatch ? I->walls[k] : P.walls[k];
+  const MatF& Mt = kBatch ? I->mf : P.mf;
   WallOut o;
   o.hit = 0;
-  const WallDev& Wl = P.walls[k];
   const double xi[3] = {x0, x1, x2};
   double nrmd[3], dnd, ps[3];
   if (!wall_geom_d(Wl, xi, (double)Rif, nrmd, &dnd, ps)) return o;
@@ -72,7 +74,7 @@ __device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, int k, int 
   const float vij[3] = {dv[0] + (rw[1] * nf[2] - rw[2] * nf[1]), dv[1] + (rw[2] * nf[0] - rw[0] * nf[2]),
                         dv[2] + (rw[0] * nf[1] - rw[1] * nf[0])};
   float F[3] = {0.f, 0.f, 0.f}, M[3] = {0.f, 0.f, 0.f};
-  law_f(nf, dnf, vij, dw, Rif, mif, P.f_Ye_pw, P.f_Ge_pw, P.f_ceta_pw, P.f_mu_pw, P.f_mur_pw, P.rolling, P.f_dt, H,
+  law_f(nf, dnf, vij, dw, Rif, mif, Mt.Ye_pw, Mt.Ge_pw, Mt.ceta_pw, Mt.mu_pw, Mt.mur_pw, P.rolling, P.f_dt, H,
         !init, Rif, F, M);
   for (int d = 0; d < 3; d++) {
     o.F[d] = F[d];
@@ -84,6 +86,7 @@ __device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, int k, int 
   return o;
 }
 
+template <bool kBatch>
 __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_constant__ Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, hc = C->hc;
@@ -133,6 +136,9 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       const int cnt = P.nbr_cnt[i];
       const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o1.x, o1.y, o1.z};
       const float Rif = o0.w;
+      // materials and walls: the context's, or those of the particle's instance in a batch
+      const InstDev* I = kBatch ? P.itab + P.inst[C->sbuf][i] : nullptr;
+      const MatF& Mt = kBatch ? I->mf : P.mf;
       // ---------------- particle-particle contacts
       // (a) Prefilter on the FP32 hi parts, 8 list entries at a time: two 16-byte loads of
       //     indices, then 8 independent 16-byte shadow loads.  hi truncates x to 24
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         const float Re = Rif * Rjf / S;
         const float mj = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rjf * Rjf * Rjf;
         const float me = mif * mj / (mif + mj);
-        law_f(nrm, dn, vij, dw, Re, me, P.f_Ye_pp, P.f_Ge_pp, P.f_ceta_pp, P.f_mu_pp, P.f_mur_pp, P.rolling, dtf, H,
+        law_f(nrm, dn, vij, dw, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp, P.rolling, dtf, H,
               !init, Rif, Ff, Mf);
         st.touch++;
         st.max_ovl = fmaxf(st.max_ovl, dn / fminf(Rif, Rjf));
@@ -239,10 +245,21 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
 
       // ---------------- particle-wall contacts (FP32 prefilter, then out of line)
       const float xf[3] = {hx[0] + lx[0], hx[1] + lx[1], hx[2] + lx[2]};
-      for (int k = 0; k < P.n_walls; k++) {
-        if (!((wall_on >> k) & 1u)) continue;
-        if (!wall_maybe_f(P.walls[k].kind, P.wf[k], xf, Rif, P.wall_margin)) continue;
-        const WallOut o = wall_contact_mixed(&P, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold, Hold, init);
+      const WallDev* WLs = kBatch ? I->walls : P.walls;
+      const WallF* WFs = kBatch ? I->wf : P.wf;
+      const int n_walls = kBatch ? I->n_walls : P.n_walls;
+      unsigned won = wall_on;
+      if (kBatch) {
+        won = 0u;
+        const double t = (double)C->step * P.dt;
+        for (int k = 0; k < n_walls; k++)
+          if (t >= WLs[k].t_on && t < WLs[k].t_off) won |= 1u << k;
+      }
+      for (int k = 0; k < n_walls; k++) {
+        if (!((won >> k) & 1u)) continue;
+        if (!wall_maybe_f(WLs[k].kind, WFs[k], xf, Rif, P.wall_margin)) continue;
+        const WallOut o = wall_contact_mixed<kBatch>(&P, I, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold,
+                                                     Hold, init);
         if (!o.hit) continue;
         for (int d = 0; d < 3; d++) {
           Ff[d] += o.F[d];
@@ -319,8 +336,11 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
 }
 
 void launch_step_mixed(const Params& P, cudaStream_t s) {
-  const int T = step_block(P.n, P.sm_count);
-  k_step_mixed<<<(P.n + T - 1) / T, T, 0, s>>>(P);
+  const int T = P.step_block > 0 ? P.step_block : step_block(P.n, P.sm_count);
+  if (P.n_inst > 1)
+    k_step_mixed<true><<<(P.n + T - 1) / T, T, 0, s>>>(P);
+  else
+    k_step_mixed<false><<<(P.n + T - 1) / T, T, 0, s>>>(P);
 }
 
 }  // namespace demgb

@@ -20,7 +20,8 @@ PRECISION = {"fp64": 0, "mixed": 1}
 EXPORTED = ["dem_workspace_bytes", "dem_create", "dem_set_walls", "dem_step", "dem_step_profiled", "dem_sync",
             "dem_get_state",
             "dem_set_state", "dem_get_forces", "dem_get_pairs", "dem_get_history", "dem_set_history",
-            "dem_get_stats", "dem_status_string", "dem_destroy", "dem_find_pairs_static"]
+            "dem_get_stats", "dem_status_string", "dem_destroy", "dem_find_pairs_static", "dem_set_instances"]
+MAX_INSTANCE_WALLS = 4
 
 
 class DemError(RuntimeError):
@@ -39,8 +40,9 @@ class Config(C.Structure):
                 ("particle", Material), ("wall", Material), ("gravity", C.c_double * 3),
                 ("dt", C.c_double), ("neighbor_factor", C.c_double), ("skin", C.c_double),
                 ("rebuild_every", C.c_int32), ("precision", C.c_int32), ("rolling_model", C.c_int32),
-                ("reserved0", C.c_int32), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
-                ("z_sink", C.c_double), ("max_overlap_ratio", C.c_double)]
+                ("n_instances", C.c_int32), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
+                ("z_sink", C.c_double), ("max_overlap_ratio", C.c_double), ("step_block", C.c_int32),
+                ("reserved1", C.c_int32)]
 
 
 class Wall(C.Structure):
@@ -48,6 +50,11 @@ class Wall(C.Structure):
                 ("normal", C.c_double * 3), ("radius", C.c_double), ("inner_radius", C.c_double),
                 ("omega", C.c_double), ("rot_origin", C.c_double * 3), ("rot_axis", C.c_double * 3),
                 ("velocity", C.c_double * 3), ("t_on", C.c_double), ("t_off", C.c_double)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("first", C.c_int64), ("particle", Material), ("wall", Material), ("n_walls", C.c_int32),
+                ("reserved0", C.c_int32), ("walls", Wall * MAX_INSTANCE_WALLS)]
 
 
 class Stats(C.Structure):
@@ -91,6 +98,7 @@ def load_library(build_if_missing: bool = True):
         "dem_get_history": [P, P, P, C.c_int64, C.POINTER(C.c_int64), P],
         "dem_set_history": [P, C.c_int64, P, P, P],
         "dem_get_stats": [P, C.POINTER(Stats)],
+        "dem_set_instances": [P, C.POINTER(Instance), C.c_int32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -141,7 +149,39 @@ def make_config(cfg: dict, n: int, radius_max: float, precision=None) -> Config:
     c.domain_hi[:] = list(cfg["domain_hi"])
     c.z_sink = cfg.get("z_sink", -1e300)
     c.max_overlap_ratio = cfg.get("max_overlap_ratio", 0.0)
+    c.n_instances = int(cfg.get("n_instances", len(cfg.get("instances", ()))))
+    c.step_block = int(cfg.get("step_block", 0))
     return c
+
+
+def _fill_wall(W, w):
+    W.kind = w["kind"]
+    W.point[:] = list(w["point"])
+    W.normal[:] = list(w["normal"])
+    W.radius = w.get("radius", 0.0)
+    W.inner_radius = w.get("inner_radius", 0.0)
+    W.omega = w.get("omega", 0.0)
+    W.rot_origin[:] = list(w.get("rot_origin", (0.0, 0.0, 0.0)))
+    W.rot_axis[:] = list(w.get("rot_axis", (0.0, 0.0, 1.0)))
+    W.velocity[:] = list(w.get("velocity", (0.0, 0.0, 0.0)))
+    W.t_on = w.get("t_on", -1e300)
+    W.t_off = w.get("t_off", 1e300)
+
+
+def make_instances(instances):
+    """dem_instance array from dicts {first, particle, wall, walls}."""
+    arr = (Instance * len(instances))()
+    for k, d in enumerate(instances):
+        I = arr[k]
+        I.first = int(d["first"])
+        I.particle = _material(d["particle"])
+        I.wall = _material(d.get("wall", d["particle"]))
+        I.n_walls = len(d["walls"])
+        if I.n_walls > MAX_INSTANCE_WALLS:
+            raise ValueError(f"instance {k}: more than {MAX_INSTANCE_WALLS} walls")
+        for w, wd in enumerate(d["walls"]):
+            _fill_wall(I.walls[w], wd)
+    return arr
 
 
 def make_walls(walls):
@@ -231,6 +271,8 @@ class DEM:
         self.n_walls = 0
         if walls:
             self.set_walls(walls)
+        if cfg.get("instances"):
+            self.set_instances(cfg["instances"])
 
     @staticmethod
     def _prep(a, dtype, shape):
@@ -255,6 +297,12 @@ class DEM:
         arr, k = make_walls(list(walls))
         _check(self.lib, "dem_set_walls", self.lib.dem_set_walls(self.h, arr, k))
         self.n_walls = k
+
+    def set_instances(self, instances):
+        """Batch contexts: per-instance particle ranges, materials and walls (dicts with keys
+        first, particle, wall, walls)."""
+        arr = make_instances(list(instances))
+        _check(self.lib, "dem_set_instances", self.lib.dem_set_instances(self.h, arr, len(instances)))
 
     def step(self, n_steps: int = 1):
         _check(self.lib, "dem_step", self.lib.dem_step(self.h, int(n_steps)))

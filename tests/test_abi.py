@@ -46,10 +46,12 @@ LAYOUT_PROG = r"""
 #include "dem.h"
 #define F(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
 int main(void) {
-  printf("dem_config %zu\ndem_wall %zu\ndem_stats %zu\ndem_material %zu\n", sizeof(dem_config),
-         sizeof(dem_wall), sizeof(dem_stats), sizeof(dem_material));
+  printf("dem_config %zu\ndem_wall %zu\ndem_stats %zu\ndem_material %zu\ndem_instance %zu\n",
+         sizeof(dem_config), sizeof(dem_wall), sizeof(dem_stats), sizeof(dem_material), sizeof(dem_instance));
   F(dem_config, radius_max) F(dem_config, gravity) F(dem_config, rebuild_every)
-  F(dem_config, domain_lo) F(dem_config, z_sink) F(dem_config, max_overlap_ratio)
+  F(dem_config, n_instances) F(dem_config, domain_lo) F(dem_config, z_sink) F(dem_config, max_overlap_ratio)
+  F(dem_config, step_block)
+  F(dem_instance, particle) F(dem_instance, wall) F(dem_instance, n_walls) F(dem_instance, walls)
   F(dem_wall, point) F(dem_wall, radius) F(dem_wall, omega) F(dem_wall, t_off)
   F(dem_stats, time) F(dem_stats, status_bits) F(dem_stats, required_workspace)
   return 0;
@@ -67,11 +69,12 @@ def test_ctypes_layout_matches_header(tmp_path):
     assert int(got["dem_wall"]) == C.sizeof(D.Wall)
     assert int(got["dem_stats"]) == C.sizeof(D.Stats)
     assert int(got["dem_material"]) == C.sizeof(D.Material)
+    assert int(got["dem_instance"]) == C.sizeof(D.Instance)
     for key, val in got.items():
         if "." not in key:
             continue
         T, f = key.split(".")
-        cls = {"dem_config": D.Config, "dem_wall": D.Wall, "dem_stats": D.Stats}[T]
+        cls = {"dem_config": D.Config, "dem_wall": D.Wall, "dem_stats": D.Stats, "dem_instance": D.Instance}[T]
         assert getattr(cls, f).offset == int(val), key
 
 
@@ -103,6 +106,13 @@ def test_workspace_bytes_and_validation(lib):
     bad_mat["particle"] = dict(bad_mat["particle"], restitution=0.0)
     c = D.make_config(bad_mat, 10, 1.5e-3)
     assert lib.dem_workspace_bytes(C.byref(c), C.byref(size)) == 1
+    # a batch needs room for its instance tables; bad batch and block settings are rejected
+    c = D.make_config(cfg_dict(n_instances=4), 1000, 1.5e-3)
+    s3 = C.c_size_t(0)
+    assert lib.dem_workspace_bytes(C.byref(c), C.byref(s3)) == 0 and s3.value > size.value
+    for bad in (dict(n_instances=-1), dict(n_instances=2000), dict(step_block=48)):
+        c = D.make_config(cfg_dict(**bad), 1000, 1.5e-3)
+        assert lib.dem_workspace_bytes(C.byref(c), C.byref(size)) == 1
 
 
 def test_create_rejects_null_arguments_without_touching_the_device(lib):
@@ -111,6 +121,7 @@ def test_create_rejects_null_arguments_without_touching_the_device(lib):
     assert lib.dem_create(C.byref(cfg), None, None, None, None, None, 0, None, C.byref(h)) == 1
     assert lib.dem_step(None, 1) == 1
     assert lib.dem_get_stats(None, None) == 1
+    assert lib.dem_set_instances(None, None, 0) == 1
 
 
 def test_status_strings(lib):

@@ -257,3 +257,104 @@ def silo(n: int = 4_300_000, seed: int | None = None, d: float = 5e-3, R: float 
                     precision=precision)
     return Workload("silo", cfg, walls, x, np.zeros((n, 3)), np.zeros((n, 3)),
                     np.full(n, r, dtype=np.float32))
+
+
+def batched_drums(n_instances: int = 512, seed: int | None = None, n_lo: int = 500, n_hi: int = 20_000,
+                  rmin: float = 1e-3, rmax: float = 3e-3, precision: str = "mixed", dt: float = 5e-6,
+                  slots=None) -> Workload:
+    """Many independent rotating drums in one batch (one context, cfg["instances"]).
+
+    Instance k is seeded with ``seed_for(4, k)`` (or ``seed + k``): particle count
+    log-uniform in [n_lo, n_hi], radii uniform in [rmin, rmax], drum speed uniform in
+    [0.5, 3] rad/s, sliding friction uniform in [0.2, 0.6], restitution uniform in
+    [0.7, 0.95]; the other material constants are those of the single drum.  Each drum has
+    the single drum's aspect L/R = 0.1/0.12 and is sized for half fill at a packing
+    fraction of 0.6 (the paper does not size them), enlarged until an FCC lattice at the
+    largest diameter holds all its spheres (radii spread over a factor 3 need about 8 %
+    more radius), filled from the bottom, axis along y, and placed in its own slot of a regular 3D grid of equal slots
+    centred on the origin, one search radius apart; every drum rotates about its own axis.
+    The drums' particles are concatenated in instance order."""
+    xs, rs, insts = [], [], []
+    specs = []
+    for k in range(n_instances):
+        rng = np.random.Generator(np.random.PCG64((seed_for(4, k) if seed is None else seed + k)))
+        nk = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        rad = rng.uniform(rmin, rmax, nk).astype(np.float32)
+        omega = float(rng.uniform(0.5, 3.0))
+        mu = float(rng.uniform(0.2, 0.6))
+        e = float(rng.uniform(0.7, 0.95))
+        solid = float(np.sum(4.0 / 3.0 * math.pi * rad.astype(np.float64) ** 3))
+        aspect = 0.1 / 0.12
+        R = (solid / (0.3 * math.pi * aspect)) ** (1.0 / 3.0)
+        # an FCC lattice at the largest diameter holds fewer spheres than a half-full drum of
+        # this size when the radii spread over 1-3 mm: grow the drum until it holds them all
+        dk = 2.0 * float(rad.max())
+        while len(_drum_sites(R, aspect * R, dk)) < nk:
+            R *= 1.03
+        specs.append((rng, nk, rad, omega, mu, e, R, aspect * R))
+    dmax = 2.0 * rmax
+    rc = 1.3 * dmax
+    Rm = max(s[6] for s in specs)
+    Lm = max(s[7] for s in specs)
+    sx, sy, sz = 2 * Rm + 2 * rc, Lm + 2 * rc, 2 * Rm + 2 * rc
+    if slots is None:
+        m = int(math.ceil(n_instances ** (1.0 / 3.0) - 1e-9))
+        slots = (m, m, int(math.ceil(n_instances / (m * m))))
+    lo = np.array([-0.5 * slots[0] * sx, -0.5 * slots[1] * sy, -0.5 * slots[2] * sz])
+    first = 0
+    for k, (rng, nk, rad, omega, mu, e, R, L) in enumerate(specs):
+        ix, iy, iz = k % slots[0], (k // slots[0]) % slots[1], k // (slots[0] * slots[1])
+        # drum axis through (cx, y0 .. y0 + L, cz)
+        cx = lo[0] + (ix + 0.5) * sx
+        y0 = lo[1] + iy * sy + rc
+        cz = lo[2] + (iz + 0.5) * sz
+        dk = 2.0 * float(rad.max())
+        pts = _drum_sites(R, L, dk)
+        pts = pts[np.argsort(pts[:, 2], kind="stable")][:nk]
+        x = pts + rng.uniform(-0.01, 0.01, pts.shape) * dk + np.array([cx, y0, cz])
+        axis = (0.0, 1.0, 0.0)
+        c = (cx, 0.0, cz)
+        walls = [cylinder(c, axis, R, omega=omega, rot_origin=c, rot_axis=axis),
+                 plane((cx, y0, cz), (0, 1, 0), omega=omega, rot_origin=c, rot_axis=axis),
+                 plane((cx, y0 + L, cz), (0, -1, 0), omega=omega, rot_origin=c, rot_axis=axis)]
+        mat = material(restitution=e, mu_slide=mu)
+        insts.append(dict(first=first, particle=mat, wall=dict(mat), walls=walls, n=nk, omega=omega,
+                          radius=R, length=L, center=c, y0=y0))
+        xs.append(x)
+        rs.append(rad)
+        first += nk
+    x = np.concatenate(xs)
+    rad = np.concatenate(rs)
+    n = len(rad)
+    hi = -lo
+    cfg = _base_cfg(domain_lo=tuple(lo), domain_hi=tuple(hi), dt=dt, particle=insts[0]["particle"],
+                    wall=dict(insts[0]["particle"]), precision=precision)
+    cfg["instances"] = insts
+    cfg["n_instances"] = n_instances
+    return Workload("batched-drums", cfg, [], x, np.zeros((n, 3)), np.zeros((n, 3)), rad)
+
+
+def _drum_sites(R, L, dk):
+    """FCC sites (spacing 1.02 dk) inside a drum of radius R and length L along y, kept
+    0.55 dk from the walls."""
+    pts = _fcc(1.02 * dk, (-R, 0.0, -R), (R, L, R))
+    rho = np.hypot(pts[:, 0], pts[:, 2])
+    inside = (rho < R - 0.55 * dk) & (pts[:, 1] > 0.55 * dk) & (pts[:, 1] < L - 0.55 * dk)
+    return pts[inside]
+
+
+def instance_workload(batch: Workload, k: int) -> Workload:
+    """Instance k of a batch as a single system (same coordinates, walls and materials), for
+    comparing the batch with plain one-system runs and with the oracle."""
+    I = batch.cfg["instances"][k]
+    lo, hi = I["first"], I["first"] + I["n"]
+    cx, y0, cz = I["center"][0], I["y0"], I["center"][2]
+    R, L = I["radius"], I["length"]
+    pad = 1.3 * 2.0 * float(batch.radius.max())
+    cfg = dict(batch.cfg)
+    cfg.pop("instances")
+    cfg.pop("n_instances")
+    cfg.update(particle=I["particle"], wall=I["wall"],
+               domain_lo=(cx - R - pad, y0 - pad, cz - R - pad), domain_hi=(cx + R + pad, y0 + L + pad, cz + R + pad))
+    return Workload(f"drum-{k}", cfg, list(I["walls"]), batch.x[lo:hi].copy(), batch.v[lo:hi].copy(),
+                    batch.w[lo:hi].copy(), batch.radius[lo:hi].copy())
