@@ -48,12 +48,13 @@ class Config(C.Structure):
                 ("wall", Material), ("gravity", C.c_double * 3), ("dt", C.c_double),
                 ("neighbor_factor", C.c_double), ("skin", C.c_double),
                 ("rebuild_every", C.c_int32), ("rolling_model", C.c_int32),
+                ("contact_model", C.c_int32), ("integrator", C.c_int32), ("linear_velocity", C.c_double),
                 ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
                 ("z_sink", C.c_double)]
 
 
 class Wall(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("point", C.c_double * 3), ("normal", C.c_double * 3),
+    _fields_ = [("kind", C.c_int32), ("translates", C.c_int32), ("point", C.c_double * 3), ("normal", C.c_double * 3),
                 ("radius", C.c_double), ("inner_radius", C.c_double), ("omega", C.c_double),
                 ("rot_origin", C.c_double * 3), ("rot_axis", C.c_double * 3),
                 ("velocity", C.c_double * 3), ("t_on", C.c_double), ("t_off", C.c_double)]
@@ -127,6 +128,8 @@ def _bind(lib):
     lib.orc_get_stats.argtypes = [P, C.POINTER(Stats)]
     lib.orc_brute_pairs.restype = C.c_int64
     lib.orc_brute_pairs.argtypes = [C.c_int64, P, P, C.c_double, P, C.c_int64]
+    lib.orc_fifth_root.restype = C.c_double
+    lib.orc_fifth_root.argtypes = [C.c_double]
     return lib
 
 
@@ -150,6 +153,9 @@ def make_config(cfg: dict, n: int) -> Config:
     c.skin = cfg.get("skin", 0.0)
     c.rebuild_every = cfg.get("rebuild_every", 0)
     c.rolling_model = cfg.get("rolling_model", 1)
+    c.contact_model = cfg.get("contact_model", 0)
+    c.integrator = cfg.get("integrator", 0)
+    c.linear_velocity = cfg.get("linear_velocity", 1.0)
     c.domain_lo[:] = list(cfg["domain_lo"])
     c.domain_hi[:] = list(cfg["domain_hi"])
     c.z_sink = cfg.get("z_sink", -1e300)
@@ -161,6 +167,7 @@ def make_walls(walls) -> tuple:
     for k, w in enumerate(walls):
         W = arr[k]
         W.kind = w["kind"]
+        W.translates = int(w.get("translates", 0))
         W.point[:] = list(w["point"])
         W.normal[:] = list(w["normal"])
         W.radius = w.get("radius", 0.0)
@@ -274,3 +281,8 @@ def brute_pairs(x, rc: float, active=None) -> np.ndarray:
     out = np.empty((max(cnt, 1), 2), dtype=np.int32)
     lib.orc_brute_pairs(n, _ptr(x), _ptr(a), float(rc), _ptr(out), cnt)
     return out[:cnt]
+
+
+def fifth_root(x: float) -> float:
+    """The oracle's x^(1/5) (Newton's method), used by the linear contact model."""
+    return float(_load().orc_fifth_root(float(x)))

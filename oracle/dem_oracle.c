@@ -14,6 +14,9 @@
  *   3. particle-particle and particle-wall contact forces (Sec. 2.1, Eqs. deltan to
  *      coulomb_overlap3, Table equation_parameters, Table rolling_torque);
  *   4. second half kick (Eq. newvv) with the accelerations of Eqs. main1 and main2.
+ * With the explicit Euler integrator (Eq. integ_EE) a step is instead v^{n+1} = v^n + a^n dt
+ * and x^{n+1} = x^n + v^n dt with the forces at (x^n, v^n), then the search when due and
+ * the forces at (x^{n+1}, v^{n+1}).
  *
  * Readings where the paper is silent (each listed in the design notes):
  *   - the torque of Eq. torque_t uses the tangential force after the Coulomb limit;
@@ -29,7 +32,13 @@
  *   - moment of inertia of a solid sphere, I = 2/5 m R^2;
  *   - the forces before the first step use the stored tangential overlap without the
  *     v_rt dt increment;
- *   - particles whose centre drops below z_sink leave the simulation.
+ *   - particles whose centre drops below z_sink leave the simulation;
+ *   - linear model: the same k and eta in the normal and tangential directions (the
+ *     paper says both directions use Eqs. linearkn and linearetan);
+ *   - viscous rolling: V_omega = (R_i w_i + R_j w_j) x n for a particle pair and
+ *     R_i (w_i - Omega) x n against a wall spinning with Omega;
+ *   - explicit Euler: every force evaluation after the first of a run adds v_rt dt to
+ *     the tangential overlap first (as in the velocity Verlet steps).
  */
 #include "dem_oracle.h"
 
@@ -90,6 +99,33 @@ static double damping_beta(double e) {
   double le = log(e);
   return le / sqrt(le * le + ORC_PI * ORC_PI);
 }
+/* 1 + (pi / ln e)^2, the denominator of Eq. linearetan (infinite for e = 1: no damping) */
+static double linear_damping_den(double e) {
+  double q = ORC_PI / log(e);
+  return 1.0 + q * q;
+}
+
+/* x^(1/5) for x > 0 by Newton's method on y^5 = x: x is scaled by 32^q into [1, 32)
+ * (exact), y_{k+1} = (4 y_k + s / y_k^4) / 5 from y_0 = 2 (above the root of the scaled
+ * value, so the iterates decrease monotonically), 12 iterations, then scaled back by 2^q.
+ * Used for the exponent 0.2 of Eq. linearkn. */
+static double fifth_root(double x) {
+  if (!(x > 0.0)) return 0.0;
+  int e;
+  double m = frexp(x, &e);       /* x = m 2^e, m in [0.5, 1) */
+  m = m * 2.0;                   /* x = m 2^(e-1), m in [1, 2) */
+  e = e - 1;
+  int q = e >= 0 ? e / 5 : -((-e + 4) / 5);
+  int r = e - 5 * q;             /* 0 <= r < 5 */
+  double sv = ldexp(m, r);       /* x = sv 32^q, sv in [1, 32) */
+  double y = 2.0;
+  for (int k = 0; k < 12; k++) {
+    double y2 = y * y;
+    double y4 = y2 * y2;
+    y = (4.0 * y + sv / y4) / 5.0;
+  }
+  return ldexp(y, q);
+}
 
 /* ------------------------------------------------------------ contact law
  * One contact of particle i with a partner (particle j or a wall), Sec. 2.1.
@@ -107,10 +143,16 @@ typedef struct {
   double Fn[3], Ft[3], nxFt[3], Mr[3], absFn;
 } contact_out;
 
+typedef struct {
+  int model;         /* 0 non-linear, 1 linear */
+  double V;          /* characteristic impact velocity of Eq. linearkn */
+  double lin_den;    /* 1 + (pi / ln e)^2 of Eq. linearetan */
+} law_opts;
+
 static void contact_law(const double* nrm, double dn, const double* vij, const double* dw,
-                        double Re, double me, double Ye, double Ge, double beta, double mu,
-                        double mu_r, int rolling, double dt, double* dt_t, int incr,
-                        contact_out* o) {
+                        const double* vomega, double Re, double me, double Ye, double Ge, double beta,
+                        double mu, double mu_r, int rolling, const law_opts* lo, double dt, double* dt_t,
+                        int incr, contact_out* o) {
   /* v_rn = (v_ij . n) n ; v_rt = v_ij - v_rn */
   double vn = dot3(vij, nrm);
   double vrn[3], vrt[3];
@@ -121,14 +163,25 @@ static void contact_law(const double* nrm, double dn, const double* vij, const d
   /* Eq. delta_t: delta_t^new = delta_t^old + v_rt dt */
   if (incr)
     for (int d = 0; d < 3; d++) dt_t[d] = dt_t[d] + vrt[d] * dt;
-  /* Eqs. nonlinearkn..nonlinearetat with S_n, S_t of Table equation_parameters */
-  double sq = sqrt(Re * dn);
-  double kn = 4.0 / 3.0 * Ye * sq;
-  double Sn = 2.0 * Ye * sq;
-  double kt = 8.0 * Ge * sq;
-  double St = 8.0 * Ge * sq;
-  double eta_n = -2.0 * sqrt(5.0 / 6.0) * beta * sqrt(Sn * me);
-  double eta_t = -2.0 * sqrt(5.0 / 6.0) * beta * sqrt(St * me);
+  double kn, kt, eta_n, eta_t;
+  if (lo->model == 0) {
+    /* Eqs. nonlinearkn..nonlinearetat with S_n, S_t of Table equation_parameters */
+    double sq = sqrt(Re * dn);
+    kn = 4.0 / 3.0 * Ye * sq;
+    double Sn = 2.0 * Ye * sq;
+    kt = 8.0 * Ge * sq;
+    double St = 8.0 * Ge * sq;
+    eta_n = -2.0 * sqrt(5.0 / 6.0) * beta * sqrt(Sn * me);
+    eta_t = -2.0 * sqrt(5.0 / 6.0) * beta * sqrt(St * me);
+  } else {
+    /* Eqs. linearkn, linearetan; the tangential constants are the same */
+    double sR = sqrt(Re);
+    double arg = 15.0 * me * lo->V * lo->V / (16.0 * sR * Ye);
+    kn = 16.0 / 15.0 * sR * Ye * fifth_root(arg);
+    eta_n = sqrt(4.0 * me * kn / lo->lin_den);
+    kt = kn;
+    eta_t = eta_n;
+  }
   /* Eq. normal_force and Eq. tangential_force */
   for (int d = 0; d < 3; d++) {
     o->Fn[d] = -(kn * dn) * nrm[d] - eta_n * vrn[d];
@@ -147,11 +200,16 @@ static void contact_law(const double* nrm, double dn, const double* vij, const d
   }
   /* Eq. torque_t: M_t = R_i n x F_t (lever applied by the caller) */
   cross3(nrm, o->Ft, o->nxFt);
-  /* Table rolling_torque, constant model: M_r = -mu_r R_e |F_n| w_hat */
+  /* Table rolling_torque: constant model M_r = -mu_r R_e |F_n| w_hat; viscous model
+     M_r = -mu_r R_e |F_n| |V_omega| w_hat */
   o->Mr[0] = o->Mr[1] = o->Mr[2] = 0.0;
   double adw = norm3(dw);
   if (rolling == 1 && adw > 0.0)
     for (int d = 0; d < 3; d++) o->Mr[d] = -mu_r * Re * aFn * dw[d] / adw;
+  if (rolling == 2 && adw > 0.0) {
+    double avw = norm3(vomega);
+    for (int d = 0; d < 3; d++) o->Mr[d] = -mu_r * Re * aFn * avw * dw[d] / adw;
+  }
   o->absFn = aFn;
 }
 
@@ -367,6 +425,8 @@ static void evaluate_forces(orc_sim* s, int incr) {
   double Ye = eff_young(&c->particle, &c->particle);
   double Ge = eff_shear(&c->particle, &c->particle);
   double beta = damping_beta(c->particle.restitution);
+  law_opts lo_pp = {c->contact_model, c->linear_velocity, linear_damping_den(c->particle.restitution)};
+  law_opts lo_pw = {c->contact_model, c->linear_velocity, linear_damping_den(c->wall.restitution)};
   double t = (double)s->step * c->dt;
   int64_t touch = 0, wtouch = 0;
   /* particle-particle contacts, list order */
@@ -398,8 +458,9 @@ static void evaluate_forces(orc_sim* s, int incr) {
     double Re = 1.0 / (1.0 / s->R[i] + 1.0 / s->R[j]);
     double me = 1.0 / (1.0 / s->m[i] + 1.0 / s->m[j]);
     contact_out o;
-    contact_law(nrm, dn, vij, dw, Re, me, Ye, Ge, beta, c->particle.mu_slide, c->particle.mu_roll,
-                c->rolling_model, c->dt, H, incr, &o);
+    /* V_omega of the viscous rolling model: (R_i w_i + R_j w_j) x n */
+    contact_law(nrm, dn, vij, dw, rwxn, Re, me, Ye, Ge, beta, c->particle.mu_slide, c->particle.mu_roll,
+                c->rolling_model, &lo_pp, c->dt, H, incr, &o);
     for (int d = 0; d < 3; d++) {
       double f = o.Fn[d] + o.Ft[d];
       s->F[3 * i + d] += f;
@@ -423,7 +484,14 @@ static void evaluate_forces(orc_sim* s, int incr) {
   for (int64_t i = 0; i < n; i++) {
     for (int k = 0; k < s->nwalls; k++) {
       double* H = &s->Hw[(i * ORC_MAX_WALLS + k) * 3];
-      const orc_wall* W = &s->walls[k];
+      /* a translating wall is where its motion has carried it by time t */
+      orc_wall Wt = s->walls[k];
+      if (Wt.translates)
+        for (int d = 0; d < 3; d++) {
+          Wt.point[d] = Wt.point[d] + Wt.velocity[d] * t;
+          Wt.rot_origin[d] = Wt.rot_origin[d] + Wt.velocity[d] * t;
+        }
+      const orc_wall* W = &Wt;
       int on = s->active[i] && t >= W->t_on && t < W->t_off;
       double nrm[3], dn, ps[3];
       if (!on || !wall_contact(W, &s->x[3 * i], s->R[i], nrm, &dn, ps)) {
@@ -441,13 +509,16 @@ static void evaluate_forces(orc_sim* s, int incr) {
         rw[d] = s->R[i] * s->w[3 * i + d];
       }
       cross3(rw, nrm, rwxn);
+      double rdw[3], vom[3];
       for (int d = 0; d < 3; d++) {
         vij[d] = (s->v[3 * i + d] - Vw[d]) + rwxn[d];
         dw[d] = s->w[3 * i + d] - Om[d];
+        rdw[d] = s->R[i] * dw[d];
       }
+      cross3(rdw, nrm, vom); /* V_omega against the wall: R_i (w_i - Omega) x n */
       contact_out o;
-      contact_law(nrm, dn, vij, dw, s->R[i], s->m[i], Yw, Gw, bw, c->wall.mu_slide, c->wall.mu_roll,
-                  c->rolling_model, c->dt, H, incr, &o);
+      contact_law(nrm, dn, vij, dw, vom, s->R[i], s->m[i], Yw, Gw, bw, c->wall.mu_slide, c->wall.mu_roll,
+                  c->rolling_model, &lo_pw, c->dt, H, incr, &o);
       for (int d = 0; d < 3; d++) {
         s->F[3 * i + d] += o.Fn[d] + o.Ft[d];
         s->M[3 * i + d] += s->R[i] * o.nxFt[d] + o.Mr[d];
@@ -487,8 +558,34 @@ static void half_kick(orc_sim* s) {
   }
 }
 
+/* Explicit Euler (Eq. integ_EE): v^{n+1} = v^n + a^n dt and x^{n+1} = x^n + v^n dt
+   (likewise for w) with the forces evaluated at (x^n, v^n) at the end of the previous
+   step, then the contact search when due and the forces at (x^{n+1}, v^{n+1}). */
+static void one_step_euler(orc_sim* s) {
+  const orc_config* c = &s->cfg;
+  for (int64_t i = 0; i < s->n; i++) {
+    if (!s->active[i]) continue;
+    for (int d = 0; d < 3; d++) {
+      double a = s->F[3 * i + d] / s->m[i] + c->gravity[d]; /* Eq. main1 */
+      double al = s->M[3 * i + d] / s->I[i];                /* Eq. main2 */
+      s->x[3 * i + d] = s->x[3 * i + d] + s->v[3 * i + d] * c->dt;
+      s->v[3 * i + d] = s->v[3 * i + d] + a * c->dt;
+      s->w[3 * i + d] = s->w[3 * i + d] + al * c->dt;
+    }
+    if (s->x[3 * i + 2] < c->z_sink) s->active[i] = 0;
+  }
+  s->step++;
+  s->since_search++;
+  if (search_due(s)) contact_search(s);
+  evaluate_forces(s, 1);
+}
+
 static void one_step(orc_sim* s) {
   const orc_config* c = &s->cfg;
+  if (c->integrator == 1) {
+    one_step_euler(s);
+    return;
+  }
   /* 1. v^{n+1/2} = v^n + a^n dt/2 ; x^{n+1} = x^n + v^{n+1/2} dt (Eq. halfstep) */
   half_kick(s);
   for (int64_t i = 0; i < s->n; i++) {
@@ -512,6 +609,9 @@ orc_sim* orc_create(const orc_config* cfg, const double* x, const double* v, con
   if (!cfg || cfg->n < 0 || !(cfg->dt > 0.0) || !(cfg->density > 0.0)) return NULL;
   if (!(cfg->particle.restitution > 0.0 && cfg->particle.restitution <= 1.0)) return NULL;
   if (!(cfg->wall.restitution > 0.0 && cfg->wall.restitution <= 1.0)) return NULL;
+  if (cfg->rolling_model < 0 || cfg->rolling_model > 2 || cfg->integrator < 0 || cfg->integrator > 1) return NULL;
+  if (cfg->contact_model < 0 || cfg->contact_model > 1) return NULL;
+  if (cfg->contact_model == 1 && !(cfg->linear_velocity > 0.0)) return NULL;
   orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
   s->cfg = *cfg;
   int64_t n = cfg->n, n1 = n > 0 ? n : 1;
@@ -729,3 +829,5 @@ int64_t orc_brute_pairs(int64_t n, const double* x, const uint8_t* active, doubl
   }
   return c;
 }
+
+double orc_fifth_root(double x) { return fifth_root(x); }

@@ -35,7 +35,12 @@ typedef struct {
   double neighbor_factor;    /* fine-search threshold r_c = factor * d_max (Sec. 3.2; 1.3 typical) */
   double skin;               /* dynamic search: rebuild when a displacement exceeds skin/2 (Sec. 3.1) */
   int32_t rebuild_every;     /* > 0: constant search mode, rebuild every n steps (Sec. 3.1) */
-  int32_t rolling_model;     /* 0: none, 1: constant rolling resistance (Table "rolling_torque") */
+  int32_t rolling_model;     /* 0: none, 1: constant, 2: viscous rolling resistance (Table
+                                "rolling_torque") */
+  int32_t contact_model;     /* 0: non-linear (Eqs. nonlinearkn..nonlinearetat), 1: linear
+                                (Eqs. linearkn, linearetan, same constants tangentially) */
+  int32_t integrator;        /* 0: velocity Verlet (Sec. 2.2), 1: explicit Euler (Eq. integ_EE) */
+  double linear_velocity;    /* characteristic impact velocity V of Eq. linearkn, m/s */
   double domain_lo[3], domain_hi[3]; /* extent of the search grid (outside points are clamped) */
   double z_sink;             /* particles whose centre falls below z_sink are removed */
 } orc_config;
@@ -44,10 +49,13 @@ typedef struct {
  * cylinder (point on axis, normal = axis, radius); 2: annulus = flat plate with a
  * circular hole (point = centre, normal, radius = outer, inner_radius = hole).
  * A wall moves with surface velocity Omega x (p - rot_origin) + velocity, Omega =
- * omega * unit(rot_axis) (Sec. 3.6, boundary motion); it exists for t_on <= t < t_off
+ * omega * unit(rot_axis) (Sec. 3.6, boundary motion); with `translates` set its geometry
+ * moves too: point and rot_origin at time t are point + velocity t and rot_origin +
+ * velocity t (translational boundary motion).  It exists for t_on <= t < t_off
  * (floating wall, Sec. 3.6). */
 typedef struct {
   int32_t kind;
+  int32_t translates;
   double point[3], normal[3];
   double radius, inner_radius;
   double omega, rot_origin[3], rot_axis[3], velocity[3];
@@ -84,6 +92,8 @@ int64_t orc_get_history(orc_sim* s, int32_t* pairs, double* dt_pair, int64_t cap
 int orc_set_history(orc_sim* s, int64_t n_pairs, const int32_t* pairs, const double* dt_pair,
                     const double* dt_wall);
 int orc_get_stats(const orc_sim* s, orc_stats* out);
+/* x^(1/5) as used by the linear contact model (exported for its pin). */
+double orc_fifth_root(double x);
 /* O(n^2) reference contact search: all i < j with |x_j - x_i|^2 < rc^2. */
 int64_t orc_brute_pairs(int64_t n, const double* x, const uint8_t* active, double rc,
                         int32_t* pairs, int64_t cap);

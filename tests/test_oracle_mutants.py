@@ -10,10 +10,11 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_variants as variants
 
 # (name, text in dem_oracle.c, replacement, pins expected to notice)
 MUTANTS = [
-    ("normal stiffness factor", "double kn = 4.0 / 3.0 * Ye * sq;", "double kn = 1.0 * Ye * sq;",
+    ("normal stiffness factor", "    kn = 4.0 / 3.0 * Ye * sq;", "    kn = 1.0 * Ye * sq;",
      ["test_static_overlap_on_plane_matches_hertz"]),
     ("Young mixing ignores the wall",
      "  double Yw = eff_young(&c->particle, &c->wall);", "  double Yw = eff_young(&c->particle, &c->particle);",
@@ -22,11 +23,11 @@ MUTANTS = [
      "double me = s->m[i];", [("test_restitution_recovers_input_coefficient", dict(e=0.7, v_rel=1.0))]),
     ("effective radius of a pair", "double Re = 1.0 / (1.0 / s->R[i] + 1.0 / s->R[j]);",
      "double Re = s->R[i];", ["test_hertz_head_on_contact_time_and_depth"]),
-    ("normal damping factor", "double eta_n = -2.0 * sqrt(5.0 / 6.0) * beta * sqrt(Sn * me);",
-     "double eta_n = -2.0 * beta * sqrt(Sn * me);", ["test_restitution_on_wall"]),
+    ("normal damping factor", "    eta_n = -2.0 * sqrt(5.0 / 6.0) * beta * sqrt(Sn * me);",
+     "    eta_n = -2.0 * beta * sqrt(Sn * me);", ["test_restitution_on_wall"]),
     ("beta without pi", "return le / sqrt(le * le + ORC_PI * ORC_PI);", "return le / sqrt(le * le + 1.0);",
      ["test_restitution_on_wall"]),
-    ("tangential stiffness factor", "double kt = 8.0 * Ge * sq;", "double kt = 4.0 * Ge * sq;",
+    ("tangential stiffness factor", "    kt = 8.0 * Ge * sq;", "    kt = 4.0 * Ge * sq;",
      ["test_tangential_stiffness_mindlin_with_rolling_coupling"]),
     ("shear-modulus mixing", "return 1.0 / (2.0 * (2.0 - a->poisson) * (1.0 + a->poisson) / a->young +",
      "return 1.0 / (1.0 * (2.0 - a->poisson) * (1.0 + a->poisson) / a->young +",
@@ -69,6 +70,25 @@ MUTANTS = [
      ["test_cylinder_static_overlap_and_drum_drag"]),
     ("annulus rim ignored", "if (rho < W->inner_radius || rho > W->radius) {", "if (rho > W->radius) {",
      ["test_annulus_face_and_rim_contact_geometry"]),
+    # the paper's variants (pins in test_oracle_variants.py)
+    ("linear stiffness exponent", "kn = 16.0 / 15.0 * sR * Ye * fifth_root(arg);",
+     "kn = 16.0 / 15.0 * sR * Ye * sqrt(arg);",
+     ["variants.test_linear_stiffness_gives_hertz_overlap_at_the_characteristic_speed"]),
+    ("linear damping drops the 4", "eta_n = sqrt(4.0 * me * kn / lo->lin_den);",
+     "eta_n = sqrt(me * kn / lo->lin_den);",
+     [("variants.test_linear_damping_recovers_the_input_restitution", dict(e=0.8))]),
+    ("linear model stiffer tangentially", "    kt = kn;\n    eta_t = eta_n;",
+     "    kt = 2.0 * kn;\n    eta_t = eta_n;", ["test_momentum_conserved_by_pair_forces",
+                                                  "variants.test_linear_tangential_stiffness_equals_normal"]),
+    ("viscous rolling without |V_omega|", "o->Mr[d] = -mu_r * Re * aFn * avw * dw[d] / adw;",
+     "o->Mr[d] = -mu_r * Re * aFn * dw[d] / adw;", ["variants.test_viscous_rolling_decays_exponentially"]),
+    ("Euler drifts with the new velocity",
+     "      s->x[3 * i + d] = s->x[3 * i + d] + s->v[3 * i + d] * c->dt;\n      s->v[3 * i + d] = s->v[3 * i + d] + a * c->dt;",
+     "      s->v[3 * i + d] = s->v[3 * i + d] + a * c->dt;\n      s->x[3 * i + d] = s->x[3 * i + d] + s->v[3 * i + d] * c->dt;",
+     ["variants.test_explicit_euler_free_fall_follows_the_discrete_recursion"]),
+    ("translating wall moves backwards", "Wt.point[d] = Wt.point[d] + Wt.velocity[d] * t;",
+     "Wt.point[d] = Wt.point[d] - Wt.velocity[d] * t;",
+     ["variants.test_translating_wall_hits_and_throws_a_resting_sphere"]),
 ]
 
 
@@ -81,7 +101,8 @@ def test_pins_kill_mutant(name, old, new, tests, tmp_path):
     with oracle.swap_library(lib):
         for t in tests:
             name_t, kw = (t, {}) if isinstance(t, str) else t
-            fn = getattr(pins, name_t)
+            mod = variants if name_t.startswith("variants.") else pins
+            fn = getattr(mod, name_t.split(".")[-1])
             try:
                 fn(**kw)
             except (AssertionError, ValueError, RuntimeError, FloatingPointError):
