@@ -81,7 +81,7 @@ typedef struct {
   int32_t rebuild_every;     /* > 0: constant search every n steps; 0: dynamic, rebuild when
                                 some |x - x_ref| > skin/2 (Sec. 3.1) */
   int32_t precision;         /* DEM_PRECISION_FP64 or DEM_PRECISION_MIXED */
-  int32_t rolling_model;     /* 0 none, 1 constant torque model (Table rolling_torque) */
+  int32_t rolling_model;     /* 0 none, 1 constant, 2 viscous torque model (Table rolling_torque) */
   int32_t n_instances;       /* 0 or 1: one system.  > 1: a batch of independent systems in
                                 one context (dem_set_instances); no counterpart in the paper */
   double domain_lo[3];       /* box of the cell grid; particles outside are clamped to */
@@ -90,7 +90,13 @@ typedef struct {
   double max_overlap_ratio;  /* > 0: DEM_ERR_OVERLAP when delta_n > ratio * R_min; 0 = off */
   int32_t step_block;        /* threads per block of the step kernel: 32, 64 or 128; 0 = chosen
                                 from n and the SM count (a launch parameter, not physics) */
+  int32_t contact_model;     /* 0 non-linear (Eqs. nonlinearkn..nonlinearetat), 1 linear
+                                (Eqs. linearkn, linearetan; same constants tangentially) */
+  int32_t integrator;        /* 0 velocity Verlet (Eqs. halfstep, newvv), 1 explicit Euler
+                                (Eq. integ_EE) */
   int32_t reserved1;
+  double linear_velocity;    /* characteristic impact velocity V of Eq. linearkn (m/s, > 0 for
+                                the linear model) */
 } dem_config;
 
 /* Analytic wall (the paper meshes the boundary; see Sec. 2.1 last paragraph and
@@ -104,12 +110,15 @@ typedef struct {
  *                     inner_radius <= rho <= radius around `point` (a silo bottom with an
  *                     orifice); nearest-point contact, including the rim of the hole.
  * Motion: the surface moves with velocity Omega x (p - rot_origin) + velocity at the
- * contact point p, Omega = omega * rot_axis / |rot_axis|; the geometry itself does not
- * move (rotation about the wall's own symmetry axis, or translation within its plane).
+ * contact point p, Omega = omega * rot_axis / |rot_axis|.  With translates = 0 the
+ * geometry itself does not move (rotation about the wall's own symmetry axis, or sliding
+ * within its plane); with translates = 1 the wall is carried by `velocity`: at time t its
+ * point and rot_origin are point + velocity t and rot_origin + velocity t (translational
+ * boundary motion, Sec. 3.6).
  * Existence: the wall acts for t_on <= t < t_off (floating wall). */
 typedef struct {
   int32_t kind;
-  int32_t reserved0;
+  int32_t translates;
   double point[3], normal[3];
   double radius, inner_radius;
   double omega, rot_origin[3], rot_axis[3], velocity[3];

@@ -79,7 +79,9 @@ dem_status derive(const dem_config* c, Derived* d) {
   if (!c || c->n <= 0 || c->n >= (1LL << 31) - 64) return DEM_ERR_ARG;
   if (!(c->density > 0.0) || !(c->radius_max > 0.0) || !(c->dt > 0.0)) return DEM_ERR_ARG;
   if (c->precision != DEM_PRECISION_FP64 && c->precision != DEM_PRECISION_MIXED) return DEM_ERR_ARG;
-  if (c->rolling_model != 0 && c->rolling_model != 1) return DEM_ERR_ARG;
+  if (c->rolling_model < 0 || c->rolling_model > 2) return DEM_ERR_ARG;
+  if (c->contact_model < 0 || c->contact_model > 1 || c->integrator < 0 || c->integrator > 1) return DEM_ERR_ARG;
+  if (c->contact_model == 1 && !(c->linear_velocity > 0.0 && std::isfinite(c->linear_velocity))) return DEM_ERR_ARG;
   if (c->n_instances < 0 || c->n_instances > c->n) return DEM_ERR_ARG;
   if (c->step_block != 0 && c->step_block != 32 && c->step_block != 64 && c->step_block != 128) return DEM_ERR_ARG;
   if (!valid_material(c->particle) || !valid_material(c->wall)) return DEM_ERR_ARG;
@@ -439,6 +441,12 @@ double eff_shear(const dem_material& a, const dem_material& b) {
                 2.0 * (2.0 - b.poisson) * (1.0 + b.poisson) / b.young);
 }
 // -2 sqrt(5/6) beta, beta = ln(e) / sqrt(ln(e)^2 + pi^2) (Table equation_parameters)
+// 1 + (pi / ln e)^2, the denominator of Eq. linearetan (infinite for e = 1: no damping)
+double linear_damping_den(double e) {
+  const double q = 3.14159265358979323846 / std::log(e);
+  return 1.0 + q * q;
+}
+
 double eta_coeff(double e) {
   double le = std::log(e);
   double beta = le / std::sqrt(le * le + 3.14159265358979323846 * 3.14159265358979323846);
@@ -456,6 +464,10 @@ void fill_materials(const dem_material& part, const dem_material& wall, MatD* md
   md->ceta_pw = eta_coeff(wall.restitution);
   md->mu_pw = wall.mu_slide;
   md->mur_pw = wall.mu_roll;
+  md->lin_den_pp = linear_damping_den(part.restitution);
+  md->lin_den_pw = linear_damping_den(wall.restitution);
+  mf->lin_den_pp = (float)md->lin_den_pp;
+  mf->lin_den_pw = (float)md->lin_den_pw;
   mf->Ye_pp = (float)md->Ye_pp;
   mf->Ge_pp = (float)md->Ge_pp;
   mf->ceta_pp = (float)md->ceta_pp;
@@ -472,6 +484,7 @@ void to_device_wall(const dem_wall& s, WallDev* W, WallF* F) {
   std::memset(W, 0, sizeof(*W));
   std::memset(F, 0, sizeof(*F));
   W->kind = s.kind;
+  W->translates = s.translates ? 1 : 0;
   double nn = std::sqrt(s.normal[0] * s.normal[0] + s.normal[1] * s.normal[1] + s.normal[2] * s.normal[2]);
   double na = std::sqrt(s.rot_axis[0] * s.rot_axis[0] + s.rot_axis[1] * s.rot_axis[1] + s.rot_axis[2] * s.rot_axis[2]);
   for (int d = 0; d < 3; d++) {
@@ -491,6 +504,7 @@ void to_device_wall(const dem_wall& s, WallDev* W, WallF* F) {
   }
   F->radius = (float)W->radius;
   F->inner = (float)W->inner;
+  for (int d = 0; d < 3; d++) F->v[d] = W->translates ? (float)W->V[d] : 0.0f;
 }
 
 void fill_walls(dem_ctx* c) {
@@ -503,6 +517,9 @@ void fill_walls(dem_ctx* c) {
     }
   }
   c->P.n_walls = c->n_walls;
+  c->P.any_translating = 0;
+  for (int k = 0; k < c->n_walls; k++)
+    if (c->P.walls[k].translates) c->P.any_translating = 1;
 }
 
 void launch_step(const Params& P, cudaStream_t s) {
@@ -712,6 +729,10 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
     P.sm_count = sms;
   }
   P.rolling = cfg->rolling_model;
+  P.contact_model = cfg->contact_model;
+  P.integrator = cfg->integrator;
+  P.lin_V = cfg->linear_velocity;
+  P.f_lin_V = (float)cfg->linear_velocity;
   P.rebuild_every = cfg->rebuild_every;
   for (int a = 0; a < 3; a++) {
     P.nc[a] = d.nc[a];
@@ -841,6 +862,7 @@ dem_status dem_set_instances(dem_ctx* c, const dem_instance* inst, int32_t n_ins
   if (n_instances != c->P.n_inst) return DEM_ERR_ARG;
   const long long n = c->P.n;
   std::vector<InstDev> tab((size_t)n_instances);
+  int any_tr = 0;
   std::vector<int> of((size_t)n);
   for (int k = 0; k < n_instances; k++) {
     const dem_instance& I = inst[k];
@@ -855,6 +877,7 @@ dem_status dem_set_instances(dem_ctx* c, const dem_instance* inst, int32_t n_ins
     for (int w = 0; w < I.n_walls; w++) {
       if (!valid_wall(I.walls[w])) return DEM_ERR_ARG;
       to_device_wall(I.walls[w], &D.walls[w], &D.wf[w]);
+      if (D.walls[w].translates) any_tr = 1;
     }
     for (long long i = lo; i < hi; i++) of[(size_t)i] = k;
   }
@@ -869,6 +892,7 @@ dem_status dem_set_instances(dem_ctx* c, const dem_instance* inst, int32_t n_ins
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));   // the host tables above go out of scope
   destroy_graph(c);
+  c->P.any_translating = any_tr;
   c->instances_set = true;
   return DEM_OK;
 }

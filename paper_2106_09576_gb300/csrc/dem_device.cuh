@@ -41,7 +41,7 @@ constexpr unsigned kStCapacity = 1u, kStNonfinite = 2u, kStOverlap = 4u, kStTime
 
 struct WallDev {
   int kind;
-  int pad;
+  int translates;   // 1: point and c move with V (translational boundary motion)
   double p[3];      // point (plane), point on axis (cylinder), centre (annulus)
   double n[3];      // unit normal / axis
   double radius, inner;
@@ -54,18 +54,20 @@ struct WallDev {
 // FP32 copies of the wall geometry for the conservative prefilter of the mixed path.
 struct WallF {
   float p[3], n[3], radius, inner;
+  float v[3];       // translation velocity when the wall translates, else 0
 };
 
 // Material constants of one contact type pair (Table equation_parameters): effective Y
 // and G, -2 sqrt(5/6) beta, sliding and rolling friction; particle-particle (_pp) and
 // particle-wall (_pw).  MatF holds their FP32 copies for the mixed path.
+// lin_den_* = 1 + (pi / ln e)^2 of Eq. linearetan (linear model).
 struct MatD {
-  double Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp;
-  double Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
+  double Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp, lin_den_pp;
+  double Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw, lin_den_pw;
 };
 struct MatF {
-  float Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp;
-  float Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw;
+  float Ye_pp, Ge_pp, ceta_pp, mu_pp, mur_pp, lin_den_pp;
+  float Ye_pw, Ge_pw, ceta_pw, mu_pw, mur_pw, lin_den_pw;
 };
 
 // One member of a batch: its materials and walls (device table indexed by instance).
@@ -113,7 +115,12 @@ struct Params {
   int precision;        // 0 FP64, 1 mixed
   int sm_count;         // SMs of the device the context runs on
   int step_block;       // threads per step-kernel block; 0 = step_block(n, sm_count)
-  int rolling;          // 0 none, 1 constant
+  int rolling;          // 0 none, 1 constant, 2 viscous (Table rolling_torque)
+  int contact_model;    // 0 non-linear, 1 linear (Eqs. linearkn, linearetan)
+  int integrator;       // 0 velocity Verlet, 1 explicit Euler (Eq. integ_EE)
+  int any_translating;  // some wall (of the context or of an instance) translates
+  double lin_V;         // characteristic impact velocity of Eq. linearkn
+  float f_lin_V;
   int rebuild_every;
   int nc[3];
   int cell_tile_shift;   // cells are ordered in columns of 2^shift x 2^shift cells (cell_index)

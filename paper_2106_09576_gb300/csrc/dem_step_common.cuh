@@ -26,10 +26,45 @@ __device__ __forceinline__ void cross3d(const double* a, const double* b, double
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+// x^(1/5) for x > 0 by Newton's method on y^5 = s after the exact scaling x = s 32^q with
+// s in [1, 32): y <- (4 y + s / y^4) / 5 from y = 2, 12 iterations, then y 2^q.  Every
+// operation rounds separately (this file is compiled without FMA contraction for the
+// FP64 kernel), so the result is the same as that of any IEEE statement of the method.
+__device__ __forceinline__ double fifth_root_d(double x) {
+  if (!(x > 0.0)) return 0.0;
+  int e;
+  double m = frexp(x, &e);
+  m = m * 2.0;
+  e = e - 1;
+  const int q = e >= 0 ? e / 5 : -((-e + 4) / 5);
+  const int r = e - 5 * q;
+  const double sv = ldexp(m, r);
+  double y = 2.0;
+  for (int k = 0; k < 12; k++) {
+    const double y2 = y * y;
+    const double y4 = y2 * y2;
+    y = (4.0 * y + sv / y4) / 5.0;
+  }
+  return ldexp(y, q);
+}
+
+// Linear model (Eqs. linearkn, linearetan): k and eta from the pair's R_e, m_e, Y_e and
+// the characteristic impact velocity V; the same constants act tangentially.
+__device__ __forceinline__ void linear_constants_d(double Re, double me, double Ye, double V, double lin_den,
+                                                   double* k, double* eta) {
+  const double sR = sqrt(Re);
+  const double arg = 15.0 * me * V * V / (16.0 * sR * Ye);
+  *k = 16.0 / 15.0 * sR * Ye * fifth_root_d(arg);
+  *eta = sqrt(4.0 * me * (*k) / lin_den);
+}
+
+// vom: V_omega of the viscous rolling model ((R_i w_i + R_j w_j) x n, or R_i (w_i - Omega)
+// x n against a wall); lin: linear model constants {V, 1 + (pi/ln e)^2} or null.
 __device__ __forceinline__ void law_d(const double* nrm, double dn, const double* vij, const double* dw,
-                                      double Re, double me, double Ye, double Ge, double ceta, double mu,
-                                      double mur, int rolling, double dt, double* H, bool incr, double* Fsum,
-                                      double* nxFt, double* Mr) {
+                                      const double* vom, double Re, double me, double Ye, double Ge,
+                                      double ceta, double mu, double mur, int rolling, const double* lin,
+                                      double dt, double* H, bool incr, double* Fsum, double* nxFt,
+                                      double* Mr) {
   double vn = dot3d(vij, nrm);
   double vrn[3], vrt[3];
   for (int d = 0; d < 3; d++) {
@@ -38,13 +73,20 @@ __device__ __forceinline__ void law_d(const double* nrm, double dn, const double
   }
   if (incr)
     for (int d = 0; d < 3; d++) H[d] = H[d] + vrt[d] * dt;
-  double sq = sqrt(Re * dn);
-  double kn = 4.0 / 3.0 * Ye * sq;
-  double Sn = 2.0 * Ye * sq;
-  double kt = 8.0 * Ge * sq;
-  double St = 8.0 * Ge * sq;
-  double eta_n = ceta * sqrt(Sn * me);
-  double eta_t = ceta * sqrt(St * me);
+  double kn, kt, eta_n, eta_t;
+  if (lin == nullptr) {
+    double sq = sqrt(Re * dn);
+    kn = 4.0 / 3.0 * Ye * sq;
+    double Sn = 2.0 * Ye * sq;
+    kt = 8.0 * Ge * sq;
+    double St = 8.0 * Ge * sq;
+    eta_n = ceta * sqrt(Sn * me);
+    eta_t = ceta * sqrt(St * me);
+  } else {
+    linear_constants_d(Re, me, Ye, lin[0], lin[1], &kn, &eta_n);
+    kt = kn;
+    eta_t = eta_n;
+  }
   double Fn[3], Ft[3];
   for (int d = 0; d < 3; d++) {
     Fn[d] = -(kn * dn) * nrm[d] - eta_n * vrn[d];
@@ -63,7 +105,22 @@ __device__ __forceinline__ void law_d(const double* nrm, double dn, const double
   double adw = sqrt(dot3d(dw, dw));
   if (rolling == 1 && adw > 0.0)
     for (int d = 0; d < 3; d++) Mr[d] = -mur * Re * aFn * dw[d] / adw;
+  if (rolling == 2 && adw > 0.0) {
+    const double avw = sqrt(dot3d(vom, vom));
+    for (int d = 0; d < 3; d++) Mr[d] = -mur * Re * aFn * avw * dw[d] / adw;
+  }
   for (int d = 0; d < 3; d++) Fsum[d] = Fn[d] + Ft[d];
+}
+
+// A translating wall where its motion has carried it by time t.
+__device__ __forceinline__ WallDev wall_at(const WallDev& W, double t) {
+  WallDev o = W;
+  if (W.translates)
+    for (int d = 0; d < 3; d++) {
+      o.p[d] = W.p[d] + W.V[d] * t;
+      o.c[d] = W.c[d] + W.V[d] * t;
+    }
+  return o;
 }
 
 // Nearest wall point and normal overlap in FP64 (same statements as the CPU reference).
@@ -151,10 +208,13 @@ __device__ __forceinline__ bool wall_maybe_f(int kind, const WallF& W, const flo
 }
 
 // ------------------------------------------------------------------ FP32 contact law
-__device__ __forceinline__ void law_f(const float* nrm, float dn, const float* vij, const float* dw, float Re,
-                                      float me, float Ye, float Ge, float ceta, float mu, float mur,
-                                      int rolling, float dt, double* H, bool incr, float Ri, float* F,
-                                      float* M) {
+// kExt: the paper's other options (linear model, viscous rolling) may occur; without it
+// they are compiled out, and the kernel keeps the registers of the default model.
+template <bool kExt>
+__device__ __forceinline__ void law_f(const float* nrm, float dn, const float* vij, const float* dw,
+                                      const float* vom, float Re, float me, float Ye, float Ge, float ceta,
+                                      float mu, float mur, int rolling, const float* lin, float dt, double* H,
+                                      bool incr, float Ri, float* F, float* M) {
   float vn = vij[0] * nrm[0] + vij[1] * nrm[1] + vij[2] * nrm[2];
   float vrn[3], vrt[3];
   for (int d = 0; d < 3; d++) {
@@ -165,12 +225,21 @@ __device__ __forceinline__ void law_f(const float* nrm, float dn, const float* v
   if (incr)
     for (int d = 0; d < 3; d++) H[d] = H[d] + f2d_int(vrt[d] * dt);
   float Hf[3] = {d2f_int(H[0]), d2f_int(H[1]), d2f_int(H[2])};
-  float sq = sqrtf(Re * dn);
-  float kn = (4.0f / 3.0f) * Ye * sq;
-  float Sn = 2.0f * Ye * sq;
-  float kt = 8.0f * Ge * sq;
-  float eta_n = ceta * sqrtf(Sn * me);
-  float eta_t = ceta * sqrtf(kt * me);
+  float kn, kt, eta_n, eta_t;
+  if (!kExt || lin == nullptr) {
+    const float sq = sqrtf(Re * dn);
+    kn = (4.0f / 3.0f) * Ye * sq;
+    const float Sn = 2.0f * Ye * sq;
+    kt = 8.0f * Ge * sq;
+    eta_n = ceta * sqrtf(Sn * me);
+    eta_t = ceta * sqrtf(kt * me);
+  } else {  // Eqs. linearkn, linearetan
+    const float sR = sqrtf(Re);
+    kn = (16.0f / 15.0f) * sR * Ye * powf(15.0f * me * lin[0] * lin[0] / (16.0f * sR * Ye), 0.2f);
+    eta_n = sqrtf(4.0f * me * kn / lin[1]);
+    kt = kn;
+    eta_t = eta_n;
+  }
   float Fn[3], Ft[3];
   for (int d = 0; d < 3; d++) {
     Fn[d] = -(kn * dn) * nrm[d] - eta_n * vrn[d];
@@ -193,7 +262,14 @@ __device__ __forceinline__ void law_f(const float* nrm, float dn, const float* v
     // unit vector of w_i - w_j, scaled first so that tiny relative spins do not underflow
     const float s = 1.0f / fmaxf(fmaxf(fabsf(dw[0]), fabsf(dw[1])), fabsf(dw[2]));
     const float u[3] = {dw[0] * s, dw[1] * s, dw[2] * s};
-    const float c = -mur * Re * aFn * rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    float c = -mur * Re * aFn * rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (int d = 0; d < 3; d++) Mr[d] = c * u[d];
+  }
+  if (kExt && rolling == 2 && (dw[0] != 0.f || dw[1] != 0.f || dw[2] != 0.f)) {
+    const float s = 1.0f / fmaxf(fmaxf(fabsf(dw[0]), fabsf(dw[1])), fabsf(dw[2]));
+    const float u[3] = {dw[0] * s, dw[1] * s, dw[2] * s};
+    const float avw = sqrtf(vom[0] * vom[0] + vom[1] * vom[1] + vom[2] * vom[2]);
+    const float c = -mur * Re * aFn * avw * rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     for (int d = 0; d < 3; d++) Mr[d] = c * u[d];
   }
   for (int d = 0; d < 3; d++) {

@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
         for (int k = 0; k < n_walls; k++)
           if (t >= WLs[k].t_on && t < WLs[k].t_off) won |= 1u << k;
       }
+      const bool lin = P.contact_model == 1;
+      const double lin_pp[2] = {P.lin_V, Mt.lin_den_pp}, lin_pw[2] = {P.lin_V, Mt.lin_den_pw};
       const double Ri = (double)RAD[i];
       const double mi = P.density * (4.0 / 3.0) * 3.14159265358979323846 * Ri * Ri * Ri;
       const double Ii = 0.4 * mi * Ri * Ri;
@@ -111,8 +113,8 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
           H[2] = Hold[ro * 3 + 2];
         }
         double f[3], nxFt[3], Mr[3];
-        law_d(nrm, dn, vij, dw, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp, P.rolling, P.dt, H, !init,
-              f, nxFt, Mr);
+        law_d(nrm, dn, vij, dw, rwxn, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp, P.rolling,
+              lin ? lin_pp : nullptr, P.dt, H, !init, f, nxFt, Mr);
         for (int d = 0; d < 3; d++) {
           F[d] += f[d];
           M[d] += Ri * nxFt[d] + Mr[d];
@@ -131,9 +133,10 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
       }
 
       // particle-wall contacts (Sec. 2.1 last paragraph; walls move per Sec. 3.6)
+      const double t_now = (double)C->step * P.dt;
       for (int k = 0; k < n_walls; k++) {
         if (!((won >> k) & 1u)) continue;
-        const WallDev& Wl = WLs[k];
+        const WallDev Wl = wall_at(WLs[k], t_now);
         double nrm[3], dn, ps[3];
         if (!wall_geom_d(Wl, xi, Ri, nrm, &dn, ps)) continue;
         const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
@@ -148,16 +151,18 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
           H[1] = Hold[ro * 3 + 1];
           H[2] = Hold[ro * 3 + 2];
         }
-        double rw[3], rwxn[3], vij[3], dw[3];
+        double rw[3], rwxn[3], vij[3], dw[3], rdw[3], vom[3];
         for (int d = 0; d < 3; d++) rw[d] = Ri * wi[d];
         cross3d(rw, nrm, rwxn);
         for (int d = 0; d < 3; d++) {
           vij[d] = (vi[d] - Vw[d]) + rwxn[d];
           dw[d] = wi[d] - Wl.Om[d];
+          rdw[d] = Ri * dw[d];
         }
+        cross3d(rdw, nrm, vom);   // V_omega against the wall: R_i (w_i - Omega) x n
         double f[3], nxFt[3], Mr[3];
-        law_d(nrm, dn, vij, dw, Ri, mi, Mt.Ye_pw, Mt.Ge_pw, Mt.ceta_pw, Mt.mu_pw, Mt.mur_pw, P.rolling, P.dt, H, !init, f,
-              nxFt, Mr);
+        law_d(nrm, dn, vij, dw, vom, Ri, mi, Mt.Ye_pw, Mt.Ge_pw, Mt.ceta_pw, Mt.mu_pw, Mt.mur_pw, P.rolling,
+              lin ? lin_pw : nullptr, P.dt, H, !init, f, nxFt, Mr);
         for (int d = 0; d < 3; d++) {
           F[d] += f[d];
           M[d] += Ri * nxFt[d] + Mr[d];
@@ -176,14 +181,16 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
       }
       P.mask[hc ^ 1][i] = mnew;
 
-      // velocity Verlet (Eqs. main1, main2, newvv, halfstep)
+      // velocity Verlet (Eqs. main1, main2, newvv, halfstep), or explicit Euler (Eq.
+      // integ_EE: the state read here is x^n, v^n, and becomes x^{n+1} = x^n + v^n dt,
+      // v^{n+1} = v^n + a^n dt)
       double xn[3], vn[3], wn[3];
       const double h = P.half_dt;
       for (int d = 0; d < 3; d++) {
         const double a = F[d] / mi + P.g[d];
         const double al = M[d] / Ii;
         double vf = vi[d], wf = wi[d];
-        if (!init) {
+        if (!init && P.integrator == 0) {
           vf = vf + a * h;
           wf = wf + al * h;
         }
@@ -193,9 +200,15 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
           P.out_F[d * n + i] = F[d];
           P.out_M[d * n + i] = M[d];
         }
-        vn[d] = vf + a * h;
-        wn[d] = wf + al * h;
-        xn[d] = xi[d] + vn[d] * P.dt;
+        if (P.integrator == 0) {
+          vn[d] = vf + a * h;
+          wn[d] = wf + al * h;
+          xn[d] = xi[d] + vn[d] * P.dt;
+        } else {
+          xn[d] = xi[d] + vi[d] * P.dt;
+          vn[d] = vi[d] + a * P.dt;
+          wn[d] = wi[d] + al * P.dt;
+        }
         Xo[d * n + i] = xn[d];
         Vo[d * n + i] = vn[d];
         Wo[d * n + i] = wn[d];

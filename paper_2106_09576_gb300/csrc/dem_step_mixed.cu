@@ -28,17 +28,22 @@ struct WallOut {
   int hit;
 };
 
-template <bool kBatch>
+template <bool kBatch, bool kExt>
 __device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstDev* I, int k, int i, int cur, double x0,
                                                    double x1, double x2, float Rif, float mif,
                                                    unsigned long long mold, const double* Hold, bool init) {
   const Params& P = *Pp;
   const WallDev& Wl = kBatch ? I->walls[k] : P.walls[k];
+
   const MatF& Mt = kBatch ? I->mf : P.mf;
   WallOut o;
   o.hit = 0;
-  const double xi[3] = {x0, x1, x2};
-  double nrmd[3], dnd, ps[3];
+  double xi[3] = {x0, x1, x2};
+  if (kExt && Wl.translates) {   // a translating wall is handled in its own frame: x - V t
+    const double tw = (double)P.ctl->step * P.dt;
+    for (int d = 0; d < 3; d++) xi[d] = xi[d] - Wl.V[d] * tw;
+  }
+  double nrmd[3], dnd, ps[3];   // ps in the wall's frame: p* - c is the same in both frames
   if (!wall_geom_d(Wl, xi, (double)Rif, nrmd, &dnd, ps)) return o;
   const int n = P.n;
   const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
@@ -73,9 +78,14 @@ __device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstD
   const float rw[3] = {Rif * wif[0], Rif * wif[1], Rif * wif[2]};
   const float vij[3] = {dv[0] + (rw[1] * nf[2] - rw[2] * nf[1]), dv[1] + (rw[2] * nf[0] - rw[0] * nf[2]),
                         dv[2] + (rw[0] * nf[1] - rw[1] * nf[0])};
+  // V_omega against the wall (viscous rolling): R_i (w_i - Omega) x n
+  const float rdw[3] = {Rif * dw[0], Rif * dw[1], Rif * dw[2]};
+  const float vom[3] = {rdw[1] * nf[2] - rdw[2] * nf[1], rdw[2] * nf[0] - rdw[0] * nf[2],
+                        rdw[0] * nf[1] - rdw[1] * nf[0]};
+  const float lin[2] = {P.f_lin_V, Mt.lin_den_pw};
   float F[3] = {0.f, 0.f, 0.f}, M[3] = {0.f, 0.f, 0.f};
-  law_f(nf, dnf, vij, dw, Rif, mif, Mt.Ye_pw, Mt.Ge_pw, Mt.ceta_pw, Mt.mu_pw, Mt.mur_pw, P.rolling, P.f_dt, H,
-        !init, Rif, F, M);
+  law_f<kExt>(nf, dnf, vij, dw, vom, Rif, mif, Mt.Ye_pw, Mt.Ge_pw, Mt.ceta_pw, Mt.mu_pw, Mt.mur_pw, P.rolling,
+        P.contact_model == 1 ? lin : nullptr, P.f_dt, H, !init, Rif, F, M);
   for (int d = 0; d < 3; d++) {
     o.F[d] = F[d];
     o.M[d] = M[d];
@@ -86,7 +96,7 @@ __device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstD
   return o;
 }
 
-template <bool kBatch>
+template <bool kBatch, bool kExt>
 __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_constant__ Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, hc = C->hc;
@@ -223,13 +233,16 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         const float dv[3] = {vif[0] - r2.x, vif[1] - r2.y, vif[2] - r2.z};
         const float dw[3] = {wif[0] - wj[0], wif[1] - wj[1], wif[2] - wj[2]};
         const float rw[3] = {Rif * wif[0] + Rjf * wj[0], Rif * wif[1] + Rjf * wj[1], Rif * wif[2] + Rjf * wj[2]};
-        const float vij[3] = {dv[0] + (rw[1] * nrm[2] - rw[2] * nrm[1]), dv[1] + (rw[2] * nrm[0] - rw[0] * nrm[2]),
-                              dv[2] + (rw[0] * nrm[1] - rw[1] * nrm[0])};
+        // (R_i w_i + R_j w_j) x n: part of v_ij, and V_omega of the viscous rolling model
+        const float rwxn[3] = {rw[1] * nrm[2] - rw[2] * nrm[1], rw[2] * nrm[0] - rw[0] * nrm[2],
+                               rw[0] * nrm[1] - rw[1] * nrm[0]};
+        const float vij[3] = {dv[0] + rwxn[0], dv[1] + rwxn[1], dv[2] + rwxn[2]};
         const float Re = Rif * Rjf / S;
         const float mj = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rjf * Rjf * Rjf;
         const float me = mif * mj / (mif + mj);
-        law_f(nrm, dn, vij, dw, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp, P.rolling, dtf, H,
-              !init, Rif, Ff, Mf);
+        const float lin[2] = {P.f_lin_V, Mt.lin_den_pp};
+        law_f<kExt>(nrm, dn, vij, dw, rwxn, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp, P.rolling,
+              P.contact_model == 1 ? lin : nullptr, dtf, H, !init, Rif, Ff, Mf);
         st.touch++;
         st.max_ovl = fmaxf(st.max_ovl, dn / fminf(Rif, Rjf));
         if (rank < kHistStride) {
@@ -255,10 +268,18 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         for (int k = 0; k < n_walls; k++)
           if (t >= WLs[k].t_on && t < WLs[k].t_off) won |= 1u << k;
       }
+      const float t_now = (float)C->step * P.f_dt;
       for (int k = 0; k < n_walls; k++) {
         if (!((won >> k) & 1u)) continue;
-        if (!wall_maybe_f(WLs[k].kind, WFs[k], xf, Rif, P.wall_margin)) continue;
-        const WallOut o = wall_contact_mixed<kBatch>(&P, I, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold,
+        // the particle seen from a translating wall's frame (v = 0 for other walls)
+        if (kExt) {
+          const float xs[3] = {xf[0] - WFs[k].v[0] * t_now, xf[1] - WFs[k].v[1] * t_now,
+                               xf[2] - WFs[k].v[2] * t_now};
+          if (!wall_maybe_f(WLs[k].kind, WFs[k], xs, Rif, P.wall_margin)) continue;
+        } else if (!wall_maybe_f(WLs[k].kind, WFs[k], xf, Rif, P.wall_margin)) {
+          continue;
+        }
+        const WallOut o = wall_contact_mixed<kBatch, kExt>(&P, I, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold,
                                                      Hold, init);
         if (!o.hit) continue;
         for (int d = 0; d < 3; d++) {
@@ -279,7 +300,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       }
       P.mask[hc ^ 1][i] = mnew;
 
-      // ---------------- velocity Verlet in FP64 with FP32 accelerations (Eqs. main1, main2)
+      // ---------------- velocity Verlet in FP64 with FP32 accelerations (Eqs. main1, main2),
+      // or explicit Euler (Eq. integ_EE: x^{n+1} = x^n + v^n dt, v^{n+1} = v^n + a^n dt)
       const float inv_m = 1.0f / mif;
       const float inv_I = 1.0f / (0.4f * mif * Rif * Rif);
       double xn[3], vn[3], wn[3];
@@ -288,7 +310,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         const double xi = X[d * n + i], vi = V[d * n + i], wi = W[d * n + i];
         const double a = f2d_int(Ff[d] * inv_m + P.f_g[d]);
         const double al = f2d_int(Mf[d] * inv_I);
-        if (init) {
+        const bool euler = kExt && P.integrator == 1;
+        if (init && !euler) {
           vn[d] = fma(a, P.half_dt, vi);
           wn[d] = fma(al, P.half_dt, wi);
         } else {
@@ -296,12 +319,12 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
           wn[d] = fma(al, P.dt, wi);
         }
         if (last) {
-          P.out_v[d * n + i] = init ? vi : fma(a, P.half_dt, vi);
-          P.out_w[d * n + i] = init ? wi : fma(al, P.half_dt, wi);
+          P.out_v[d * n + i] = (init || euler) ? vi : fma(a, P.half_dt, vi);
+          P.out_w[d * n + i] = (init || euler) ? wi : fma(al, P.half_dt, wi);
           P.out_F[d * n + i] = f2d_int(Ff[d]);
           P.out_M[d * n + i] = f2d_int(Mf[d]);
         }
-        xn[d] = fma(vn[d], P.dt, xi);
+        xn[d] = fma(euler ? vi : vn[d], P.dt, xi);
         P.x[nxt][d * n + i] = xn[d];
         P.v[nxt][d * n + i] = vn[d];
         P.w[nxt][d * n + i] = wn[d];
@@ -337,10 +360,21 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
 
 void launch_step_mixed(const Params& P, cudaStream_t s) {
   const int T = P.step_block > 0 ? P.step_block : step_block(P.n, P.sm_count);
-  if (P.n_inst > 1)
-    k_step_mixed<true><<<(P.n + T - 1) / T, T, 0, s>>>(P);
-  else
-    k_step_mixed<false><<<(P.n + T - 1) / T, T, 0, s>>>(P);
+  const int blocks = (P.n + T - 1) / T;
+  // the paper's other options (linear model, viscous rolling, explicit Euler, translating
+  // walls) run in their own instantiation, so the default one keeps its registers
+  const bool ext = P.contact_model != 0 || P.rolling == 2 || P.integrator != 0 || P.any_translating;
+  if (P.n_inst > 1) {
+    if (ext)
+      k_step_mixed<true, true><<<blocks, T, 0, s>>>(P);
+    else
+      k_step_mixed<true, false><<<blocks, T, 0, s>>>(P);
+  } else {
+    if (ext)
+      k_step_mixed<false, true><<<blocks, T, 0, s>>>(P);
+    else
+      k_step_mixed<false, false><<<blocks, T, 0, s>>>(P);
+  }
 }
 
 }  // namespace demgb

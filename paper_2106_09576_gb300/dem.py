@@ -42,11 +42,12 @@ class Config(C.Structure):
                 ("rebuild_every", C.c_int32), ("precision", C.c_int32), ("rolling_model", C.c_int32),
                 ("n_instances", C.c_int32), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
                 ("z_sink", C.c_double), ("max_overlap_ratio", C.c_double), ("step_block", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("contact_model", C.c_int32), ("integrator", C.c_int32), ("reserved1", C.c_int32),
+                ("linear_velocity", C.c_double)]
 
 
 class Wall(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("reserved0", C.c_int32), ("point", C.c_double * 3),
+    _fields_ = [("kind", C.c_int32), ("translates", C.c_int32), ("point", C.c_double * 3),
                 ("normal", C.c_double * 3), ("radius", C.c_double), ("inner_radius", C.c_double),
                 ("omega", C.c_double), ("rot_origin", C.c_double * 3), ("rot_axis", C.c_double * 3),
                 ("velocity", C.c_double * 3), ("t_on", C.c_double), ("t_off", C.c_double)]
@@ -151,11 +152,15 @@ def make_config(cfg: dict, n: int, radius_max: float, precision=None) -> Config:
     c.max_overlap_ratio = cfg.get("max_overlap_ratio", 0.0)
     c.n_instances = int(cfg.get("n_instances", len(cfg.get("instances", ()))))
     c.step_block = int(cfg.get("step_block", 0))
+    c.contact_model = int(cfg.get("contact_model", 0))
+    c.integrator = int(cfg.get("integrator", 0))
+    c.linear_velocity = float(cfg.get("linear_velocity", 1.0))
     return c
 
 
 def _fill_wall(W, w):
     W.kind = w["kind"]
+    W.translates = int(w.get("translates", 0))
     W.point[:] = list(w["point"])
     W.normal[:] = list(w["normal"])
     W.radius = w.get("radius", 0.0)
@@ -187,18 +192,7 @@ def make_instances(instances):
 def make_walls(walls):
     arr = (Wall * max(1, len(walls)))()
     for k, w in enumerate(walls):
-        W = arr[k]
-        W.kind = w["kind"]
-        W.point[:] = list(w["point"])
-        W.normal[:] = list(w["normal"])
-        W.radius = w.get("radius", 0.0)
-        W.inner_radius = w.get("inner_radius", 0.0)
-        W.omega = w.get("omega", 0.0)
-        W.rot_origin[:] = list(w.get("rot_origin", (0.0, 0.0, 0.0)))
-        W.rot_axis[:] = list(w.get("rot_axis", (0.0, 0.0, 1.0)))
-        W.velocity[:] = list(w.get("velocity", (0.0, 0.0, 0.0)))
-        W.t_on = w.get("t_on", -1e300)
-        W.t_off = w.get("t_off", 1e300)
+        _fill_wall(arr[k], w)
     return arr, len(walls)
 
 
