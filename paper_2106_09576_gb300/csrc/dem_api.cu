@@ -480,7 +480,7 @@ void fill_materials(const dem_material& part, const dem_material& wall, MatD* md
   mf->mur_pw = (float)md->mur_pw;
 }
 
-void to_device_wall(const dem_wall& s, WallDev* W, WallF* F) {
+void to_device_wall(const dem_wall& s, WallDev* W, WallF* F, float* fv) {
   std::memset(W, 0, sizeof(*W));
   std::memset(F, 0, sizeof(*F));
   W->kind = s.kind;
@@ -504,16 +504,17 @@ void to_device_wall(const dem_wall& s, WallDev* W, WallF* F) {
   }
   F->radius = (float)W->radius;
   F->inner = (float)W->inner;
-  for (int d = 0; d < 3; d++) F->v[d] = W->translates ? (float)W->V[d] : 0.0f;
+  for (int d = 0; d < 3; d++) fv[d] = W->translates ? (float)W->V[d] : 0.0f;
 }
 
 void fill_walls(dem_ctx* c) {
   for (int k = 0; k < kMaxWalls; k++) {
     if (k < c->n_walls) {
-      to_device_wall(c->walls[k], &c->P.walls[k], &c->P.wf[k]);
+      to_device_wall(c->walls[k], &c->P.walls[k], &c->P.wf[k], c->P.wf_v[k]);
     } else {
       std::memset(&c->P.walls[k], 0, sizeof(WallDev));
       std::memset(&c->P.wf[k], 0, sizeof(WallF));
+      for (int d = 0; d < 3; d++) c->P.wf_v[k][d] = 0.0f;
     }
   }
   c->P.n_walls = c->n_walls;
@@ -876,7 +877,7 @@ dem_status dem_set_instances(dem_ctx* c, const dem_instance* inst, int32_t n_ins
     D.n_walls = I.n_walls;
     for (int w = 0; w < I.n_walls; w++) {
       if (!valid_wall(I.walls[w])) return DEM_ERR_ARG;
-      to_device_wall(I.walls[w], &D.walls[w], &D.wf[w]);
+      to_device_wall(I.walls[w], &D.walls[w], &D.wf[w], D.wf_v[w]);
       if (D.walls[w].translates) any_tr = 1;
     }
     for (long long i = lo; i < hi; i++) of[(size_t)i] = k;

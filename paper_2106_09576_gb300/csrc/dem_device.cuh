@@ -52,9 +52,8 @@ struct WallDev {
 };
 
 // FP32 copies of the wall geometry for the conservative prefilter of the mixed path.
-struct WallF {
+struct WallF {     // 32 bytes: the prefilter reads it for every particle
   float p[3], n[3], radius, inner;
-  float v[3];       // translation velocity when the wall translates, else 0
 };
 
 // Material constants of one contact type pair (Table equation_parameters): effective Y
@@ -79,6 +78,7 @@ struct InstDev {
   int pad;
   WallDev walls[kMaxInstWalls];
   WallF wf[kMaxInstWalls];
+  float wf_v[kMaxInstWalls][3];   // FP32 translation velocity of translating walls, else 0
 };
 
 // Device-resident control block: everything that changes from step to step.
@@ -142,6 +142,7 @@ struct Params {
   MatF mf;
   long long z_sink_key;   // ordered-integer image of z_sink (exact comparison without FP64)
   WallF wf[kMaxWalls];
+  float wf_v[kMaxWalls][3];   // FP32 translation velocity of translating walls, else 0
   // batch (n_inst > 1): per-instance materials and walls replace md, mf, walls, wf
   int n_inst;
   const InstDev* itab;  // [n_inst]

@@ -273,8 +273,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         if (!((won >> k) & 1u)) continue;
         // the particle seen from a translating wall's frame (v = 0 for other walls)
         if (kExt) {
-          const float xs[3] = {xf[0] - WFs[k].v[0] * t_now, xf[1] - WFs[k].v[1] * t_now,
-                               xf[2] - WFs[k].v[2] * t_now};
+          const float* wv = kBatch ? I->wf_v[k] : P.wf_v[k];
+          const float xs[3] = {xf[0] - wv[0] * t_now, xf[1] - wv[1] * t_now, xf[2] - wv[2] * t_now};
           if (!wall_maybe_f(WLs[k].kind, WFs[k], xs, Rif, P.wall_margin)) continue;
         } else if (!wall_maybe_f(WLs[k].kind, WFs[k], xf, Rif, P.wall_margin)) {
           continue;
