@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["silo", "drum"], default="silo")
+    p.add_argument("--workload", choices=["silo", "drum", "dam"], default="silo")
     p.add_argument("--n", type=int, default=None, help="override the particle count (smaller runs)")
     p.add_argument("--fp64-steps", type=int, default=None)
     p.add_argument("--profile-steps", type=int, default=None)
@@ -68,6 +68,12 @@ def make_workload(name, n=None, precision="mixed"):
     if name == "silo":
         wl = workloads.silo(n=n or 4_300_000, precision=precision, spacing=0.995, jitter=0.002)
         desc = "silo-packed"
+    elif name == "dam":
+        # the weak-scaling dam break at 1.6M spheres (a 0.1 m slab), packed behind the dam
+        # (touching lattice), the dam gone after 500 steps
+        wl = workloads.dam_break(n=n or 1_600_000, precision=precision, t_dam=0.002, spacing=0.999,
+                                 jitter=0.002)
+        desc = "dam-break"
     else:
         wl = workloads.drum(n=n or 200_000, precision=precision, spacing=0.999)
         desc = "drum-rotating"

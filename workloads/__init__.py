@@ -358,3 +358,41 @@ def instance_workload(batch: Workload, k: int) -> Workload:
                domain_lo=(cx - R - pad, y0 - pad, cz - R - pad), domain_hi=(cx + R + pad, y0 + L + pad, cz + R + pad))
     return Workload(f"drum-{k}", cfg, list(I["walls"]), batch.x[lo:hi].copy(), batch.v[lo:hi].copy(),
                     batch.w[lo:hi].copy(), batch.radius[lo:hi].copy())
+
+
+def dam_break(n: int = 160_000, seed: int | None = None, d: float = 1e-3, length: float = 0.2,
+              height: float = 0.3, t_dam: float = 0.05, precision: str = "mixed", spacing: float = 1.05,
+              jitter: float = 0.02, depth: float | None = None) -> Workload:
+    """Dam break, the paper's weak-scaling case: monodisperse spheres fill the left half of
+    a box (x in [0, length], z up to height) behind a floating wall (the dam, at
+    x = length / 2) that disappears at t_dam; the depth (y) grows with the particle count,
+    0.01 m per 160,000 spheres, as in the paper's weak-scaling table.  The paper gives
+    neither the sphere size nor the box length and height: d = 1 mm and a 0.2 m x 0.2 m
+    cross-section hold the 160,000 spheres of a 0.01 m slab about 0.14 m high.  Filled on a
+    jittered cubic lattice at `spacing` d from the floor; material of the 1,000-sphere
+    cube; dt = 4e-6 s (about a tenth of the Rayleigh time of a 1 mm sphere)."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(6) if seed is None else seed))
+    if depth is None:
+        depth = max(0.01 * n / 160_000, 4.0 * d)
+    r = 0.5 * d
+    a = spacing * d
+    half = 0.5 * length
+    nx = int(math.floor((half - d) / a))
+    ny = max(1, int(math.floor((depth - d) / a)))
+    per_layer = nx * ny
+    layers = int(math.ceil(n / per_layer))
+    X, Y = np.meshgrid(r + 0.5 * (d - a) + a * (np.arange(nx) + 0.5), r + 0.5 * (d - a) + a * (np.arange(ny) + 0.5),
+                       indexing="ij")
+    x = np.empty((layers * per_layer, 3))
+    x[:, 0] = np.tile(X.ravel(), layers)
+    x[:, 1] = np.tile(Y.ravel(), layers)
+    x[:, 2] = np.repeat(r + 0.5 * (a - d) + np.arange(layers) * a, per_layer)
+    if x[:n, 2].max() > height - r:
+        raise RuntimeError("dam break: the box is too low for this many spheres")
+    x = x[:n] + rng.uniform(-jitter, jitter, (n, 3)) * d
+    walls = box_walls((0.0, 0.0, 0.0), (length, depth, height))
+    walls.append(plane((half, 0.0, 0.0), (-1.0, 0.0, 0.0), t_off=t_dam))   # the dam
+    cfg = _base_cfg(domain_lo=(0.0, 0.0, 0.0), domain_hi=(length, depth, height), dt=4e-6,
+                    precision=precision)
+    return Workload("dam-break", cfg, walls, x, np.zeros((n, 3)), np.zeros((n, 3)),
+                    np.full(n, r, dtype=np.float32))
