@@ -1,6 +1,7 @@
-"""Builds libdem_gb300.so (the CUDA library behind include/dem.h) in-tree for sm_103a.
+"""Builds libdem_gb300.so (the CUDA library behind include/dem.h and include/surrogate.h)
+in-tree for sm_103a.
 
-Four translation units are compiled in parallel with nvcc, then linked as one shared
+The translation units are compiled in parallel with nvcc, then linked as one shared
 library in paper_2106_09576_gb300/_build/.  The FP64 step kernel is compiled without
 FMA contraction so that it rounds like the serial CPU statement of the method.
 """
@@ -25,6 +26,7 @@ SOURCES = {
     # additions, multiplications and FMAs stay IEEE (the double-float arithmetic needs them)
     "dem_step_mixed.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "dem_static_pairs.cu": [],
+    "surrogate.cu": [],
 }
 
 
@@ -38,6 +40,7 @@ def nvcc() -> str:
 def _inputs():
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(ROOT, "include", "dem.h"))
+    deps.append(os.path.join(ROOT, "include", "surrogate.h"))
     deps.append(os.path.abspath(__file__))
     return deps
 

@@ -22,10 +22,10 @@ def lib():
     return D.load_library()
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER, prefix="dem_"):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(dem_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(" + prefix + r"[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_function_is_exported(lib):
@@ -38,6 +38,12 @@ def test_every_declared_function_is_exported(lib):
     for n in names:
         assert hasattr(lib, n)
     assert sorted(D.EXPORTED) == names
+    # the surrogate's entry points (include/surrogate.h)
+    from paper_2106_09576_gb300 import surrogate as SG
+    snames = declared_functions(os.path.join(ROOT, "include", "surrogate.h"), "surr_")
+    assert len(snames) >= 12 and sorted(SG.SURR_FUNCS) == snames
+    sexported = set(re.findall(r" T (surr_[a-z0-9_]+)", out))
+    assert not [n for n in snames if n not in sexported]
 
 
 LAYOUT_PROG = r"""
