@@ -7,10 +7,11 @@
  * Network (hidden width H = 128, BF16 weights and activations, FP32 accumulation):
  *   h0 = relu(X W0 + b0)                          node encoder, X [N][16]
  *   m  = relu([h0[i] | E] W1 + b1)                 per directed edge i <- j, E [nE][16]
- *   a  = sum over the edges into i of m            (segment sum over a receiver-sorted CSR)
+ *   a  = c * sum over the edges into i of m        (segment sum over a receiver-sorted CSR)
  *   h1 = h0 + relu([h0 | a] W2 + b2)
- *   s  = sum over neighbours j of h1[j];  h2 = h1 + relu([h1 | s] W3 + b3)
- *   s  = sum over neighbours j of h2[j];  h3 = h2 + relu([h2 | s] W4 + b4)
+ *   s  = c * sum over neighbours j of h1[j];  h2 = h1 + relu([h1 | s] W3 + b3)
+ *   s  = c * sum over neighbours j of h2[j];  h3 = h2 + relu([h2 | s] W4 + b4)
+ * with c = SURR_AGG_SCALE, so that sums over a dozen neighbours keep the activations' size.
  *   Y  = h3 W5 + b5                                Y [N][8] (6 outputs used)
  * Parameters live in one FP32 array (the master copy the optimiser updates) and one BF16
  * copy for the tensor-core products, both at the offsets of surr_param_layout.
@@ -30,6 +31,7 @@ extern "C" {
 #define SURR_NODE_IN 16
 #define SURR_EDGE_IN 16
 #define SURR_OUT 8
+#define SURR_AGG_SCALE 0.125f
 
 /* Offsets (in elements) of the parameter tensors in the flat arrays, and the total:
  * W0 [16][128] b0 [128] W1 [144][128] b1 [128] W2 [256][128] b2 [128] W3 [256][128] b3 [128]
@@ -75,7 +77,8 @@ int surr_adam(float* params, void* params_bf16, const float* grad, float* m, flo
  * y0 + L, radius Rd, length scale d0, velocity scale vs.  Node features X [n][16]: v / vs,
  * w R / vs, 2R / d0, position in the drum frame, distances to the mantle and the caps
  * (in d0, clipped to 5), 1.  Edge features E [n_edges][16]: (x_j - x_i) / d0, |x_j - x_i| /
- * d0, (R_i + R_j - |x_j - x_i|) / d0, (v_j - v_i) / vs, (w_j R_j - w_i R_i) / vs.
+ * d0, the overlap max(R_i + R_j - |x_j - x_i|, 0) in units of 0.01 d0, (v_j - v_i) / vs,
+ * (w_j R_j - w_i R_i) / vs.
  * recv_scratch holds n_edges ints (the receiver of each edge). */
 int surr_features(const double* x, const double* v, const double* w, const float* radius, int64_t n,
                   const int32_t* row_ptr, const int32_t* col, int64_t n_edges, const double* geom,

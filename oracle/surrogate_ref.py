@@ -6,10 +6,10 @@ GPU path.  Written from the network's definition (include/surrogate.h):
 
   h0 = relu(X W0 + b0)
   m_e = relu([h0[recv(e)] | E_e] W1 + b1)          e = an edge j -> i, recv(e) = i
-  a_i = sum of m_e over the edges into i
+  a_i = c * (sum of m_e over the edges into i)      c = 0.125
   h1 = h0 + relu([h0 | a] W2 + b2)
-  h2 = h1 + relu([h1 | s1] W3 + b3),  s1_i = sum of h1_j over the neighbours j of i
-  h3 = h2 + relu([h2 | s2] W4 + b4),  s2_i = sum of h2_j over the neighbours j of i
+  h2 = h1 + relu([h1 | s1] W3 + b3),  s1_i = c * (sum of h1_j over the neighbours j of i)
+  h3 = h2 + relu([h2 | s2] W4 + b4),  s2_i = c * (sum of h2_j over the neighbours j of i)
   Y  = h3 W5 + b5
 
 With `bf16=True` the values the GPU stores in BF16 (inputs, weights, activations, sums) are
@@ -21,6 +21,7 @@ the gradient is pinned against central finite differences (tests/test_surrogate_
 import numpy as np
 
 H, FIN, EIN, NOUT = 128, 16, 16, 8
+AGG = 0.125          # the scale of every neighbour or edge sum
 SHAPES = [(FIN, H), (H + EIN, H), (2 * H, H), (2 * H, H), (2 * H, H), (H, NOUT)]
 
 
@@ -81,7 +82,7 @@ def forward(p, X, E, row_ptr, col, bf16=True):
     c["u1"] = r(np.maximum(z1, 0))
     a = np.zeros((n, H))
     np.add.at(a, recv, c["u1"])
-    c["a"] = r(a)
+    c["a"] = r(AGG * a)
     z2 = np.concatenate([c["h0"], c["a"]], axis=1) @ Wr[2] + bs[2]
     u2 = np.maximum(z2, 0)
     c["u2"] = r(u2)
@@ -90,7 +91,7 @@ def forward(p, X, E, row_ptr, col, bf16=True):
     for l, (sk, uk, hk) in zip((3, 4), (("s1", "u3", "h2"), ("s2", "u4", "h3"))):
         s = np.zeros((n, H))
         np.add.at(s, recv, hs[col])
-        c[sk] = r(s)
+        c[sk] = r(AGG * s)
         z = np.concatenate([hs, c[sk]], axis=1) @ Wr[l] + bs[l]
         u = np.maximum(z, 0)
         c[uk] = r(u)
@@ -120,7 +121,7 @@ def backward(p, dY, c, row_ptr, col):
         A = np.concatenate([c[hin], c[sk]], axis=1)
         put(l, A.T @ dz, dz.sum(0))
         dA = dz @ Wr[l].T
-        ds = dA[:, H:]
+        ds = AGG * dA[:, H:]
         dns = np.zeros((n, H))
         np.add.at(dns, col, ds[recv])     # transpose of the neighbour sum
         dh = dh + dA[:, :H] + dns
@@ -130,7 +131,7 @@ def backward(p, dY, c, row_ptr, col):
     dA = dz @ Wr[2].T
     dh0 = dh + dA[:, :H]
     da = dA[:, H:]
-    dz1 = da[recv] * (c["u1"] > 0)
+    dz1 = AGG * da[recv] * (c["u1"] > 0)
     A1 = np.concatenate([c["h0"][recv], c["E"]], axis=1)
     put(1, A1.T @ dz1, dz1.sum(0))
     dA1 = dz1 @ Wr[1].T

@@ -21,6 +21,7 @@ constexpr int FIN = SURR_NODE_IN;
 constexpr int EIN = SURR_EDGE_IN;
 constexpr int NOUT = SURR_OUT;
 constexpr int kSplit = 64;   // reduction chunks of a weight-gradient product
+constexpr float kAgg = SURR_AGG_SCALE;
 
 __device__ float g_mse_part[256];   // partial sums of surr_mse (one call at a time per device)
 
@@ -177,9 +178,9 @@ __global__ void k_to_bf16(const float* src, bf16* dst, int64_t count) {
 // out[i] = sum over the CSR row i of src[g(e)] (g = col for a neighbour sum, the edge
 // itself for an edge sum), source rows ld_src apart; FP32 accumulation in row order; one
 // warp per row, 4 of the H columns per lane.  Writes BF16 and/or FP32 (adding to the FP32
-// output when `accumulate` is set).
+// output when `accumulate` is set), times `scale` (SURR_AGG_SCALE for the network's sums).
 __global__ void k_segsum(const int* row_ptr, const int* col, const bf16* src_b, const float* src_f, int64_t ld_src,
-                         int64_t n, bf16* out_b, float* out_f, int accumulate) {
+                         int64_t n, bf16* out_b, float* out_f, int accumulate, float scale) {
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -193,8 +194,9 @@ __global__ void k_segsum(const int* row_ptr, const int* col, const bf16* src_b, 
   }
   for (int q = 0; q < 4; q++) {
     const int64_t idx = i * H + lane * 4 + q;
-    if (out_b) out_b[idx] = __float2bfloat16(s[q]);
-    if (out_f) out_f[idx] = accumulate ? out_f[idx] + s[q] : s[q];
+    const float v = scale * s[q];
+    if (out_b) out_b[idx] = __float2bfloat16(v);
+    if (out_f) out_f[idx] = accumulate ? out_f[idx] + v : v;
   }
 }
 
@@ -206,7 +208,7 @@ __global__ void k_gather_mask(const float* da, const int32_t* recv, const bf16* 
   if (e >= nE * H) return;
   const int64_t m = e / H;
   const int h = (int)(e % H);
-  float d = da[(int64_t)recv[m] * H + h];
+  float d = kAgg * da[(int64_t)recv[m] * H + h];
   if (!(__bfloat162float(u[e]) > 0.0f)) d = 0.0f;
   dz_b[e] = __float2bfloat16(d);
   dz_f[e] = d;
@@ -480,7 +482,7 @@ __global__ void k_edge_features(const double* x, const double* v, const double* 
     o[8 + d] = (float)((w[3 * j + d] * rad[j] - w[3 * i + d] * rad[i]) / vs);
   }
   o[3] = (float)(r / d0);
-  o[4] = (float)(((double)rad[i] + (double)rad[j] - r) / d0);
+  o[4] = (float)(100.0 * fmax((double)rad[i] + (double)rad[j] - r, 0.0) / d0);   // overlap, in 0.01 d0
   for (int d = 11; d < EIN; d++) o[d] = 0.0f;
 }
 
@@ -576,14 +578,14 @@ extern "C" int surr_forward(const void* params_bf16, const float* params, const 
     gemm(CatA{w.h0, w.recv, H, w.Eb, EIN}, MatB{Pb + L.W[1], H, 0}, nE, H, H + EIN, w.C, s);
     k_epilogue<<<nblk(nE * H, T), T, 0, s>>>(w.C, params + L.b[1], nE, H, 1, nullptr, nullptr, w.u1, nullptr);
   }
-  k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, nullptr, w.u1, nullptr, H, n, w.a, nullptr, 0);
+  k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, nullptr, w.u1, nullptr, H, n, w.a, nullptr, 0, kAgg);
   gemm(CatA{w.h0, nullptr, H, w.a, H}, MatB{Pb + L.W[2], H, 0}, n, H, 2 * H, w.C, s);
   k_epilogue<<<nblk(n * H, T), T, 0, s>>>(w.C, params + L.b[2], n, H, 1, w.h0, w.u2, w.h1, nullptr);
   // two node layers on neighbour sums
-  k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, w.h1, nullptr, H, n, w.s1, nullptr, 0);
+  k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, w.h1, nullptr, H, n, w.s1, nullptr, 0, kAgg);
   gemm(CatA{w.h1, nullptr, H, w.s1, H}, MatB{Pb + L.W[3], H, 0}, n, H, 2 * H, w.C, s);
   k_epilogue<<<nblk(n * H, T), T, 0, s>>>(w.C, params + L.b[3], n, H, 1, w.h1, w.u3, w.h2, nullptr);
-  k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, w.h2, nullptr, H, n, w.s2, nullptr, 0);
+  k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, w.h2, nullptr, H, n, w.s2, nullptr, 0, kAgg);
   gemm(CatA{w.h2, nullptr, H, w.s2, H}, MatB{Pb + L.W[4], H, 0}, n, H, 2 * H, w.C, s);
   k_epilogue<<<nblk(n * H, T), T, 0, s>>>(w.C, params + L.b[4], n, H, 1, w.h2, w.u4, w.h3, nullptr);
   // decoder
@@ -619,7 +621,7 @@ extern "C" int surr_backward(const void* params_bf16, const float* dY, const int
     // graph is symmetric, so the transpose of the neighbour sum is the neighbour sum
     gemm(CatA{w.dzb, nullptr, H, nullptr, 0}, MatB{Pb + L.W[l], H, 1}, n, 2 * H, H, w.C, s);
     k_add_cols<<<nblk(n * H, T), T, 0, s>>>(w.dh, w.C, 2 * H, n, H);
-    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, nullptr, w.C + H, 2 * H, n, nullptr, w.dh, 1);
+    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, nullptr, w.C + H, 2 * H, n, nullptr, w.dh, 1, kAgg);
   }
   // ---- layer 2: h1 = h0 + u2, u2 = relu([h0 | a] W2 + b2), a = sum of the edge messages
   k_relu_back<<<nblk(n * H, T), T, 0, s>>>(w.dh, H, w.u2, n, H, 1, w.dzb, w.dzf);
@@ -636,7 +638,7 @@ extern "C" int surr_backward(const void* params_bf16, const float* dY, const int
     k_colsum<<<H, 256, 0, s>>>(w.dzf, nE, H, grad + L.b[1]);
     gemm(CatA{w.dzb, nullptr, H, nullptr, 0}, MatB{Pb + L.W[1], H, 1}, nE, H + EIN, H, w.C, s);
     // dh0[i] += sum over the edges into i of d[e, :H]
-    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, nullptr, nullptr, w.C, H + EIN, n, nullptr, w.dh, 1);
+    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, nullptr, nullptr, w.C, H + EIN, n, nullptr, w.dh, 1, 1.0f);
   } else {
     cudaMemsetAsync(grad + L.W[1], 0, (size_t)(L.b[1] - L.W[1] + H) * 4, s);
   }

@@ -186,3 +186,130 @@ def drum_geometry(wl, device):
     omega = abs(wl.walls[0].get("omega", 1.0)) or 1.0
     d0 = 2.0 * float(wl.radius.max())
     return torch.tensor([0.0, 0.0, 0.0, R, L, d0, omega * R, 0.0], dtype=torch.float64, device=device)
+
+
+# ------------------------------------------------------------------ data, training, rollout
+class Sample:
+    __slots__ = ("graph", "X", "E", "T")
+
+    def __init__(self, graph, X, E, T):
+        self.graph, self.X, self.E, self.T = graph, X, E, T
+
+
+def _state(dem_ctx, n, dev):
+    import torch
+    x = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    v = torch.empty_like(x)
+    w = torch.empty_like(x)
+    a = torch.empty(n, dtype=torch.uint8, device=dev)
+    dem_ctx.state((x, v, w, a))
+    return x, v, w
+
+
+def drum_trajectories(n_traj, n_particles, settle_steps, samples_per_traj, gap_steps, net, device="cuda",
+                      seed0=None, omega=1.0):
+    """Training samples from DEM runs of small rotating drums (the 200k drum's materials,
+    radii and speed, scaled down; seeded per trajectory with seed_for(5, t)).  After
+    settling, every gap_steps steps: the graph and features of a state and the increments
+    over the next K_STEPS steps.  Targets are scaled by net.out_scale."""
+    import torch
+    import workloads
+    from .dem import DEM
+    dev = torch.device(device)
+    out = []
+    for t in range(n_traj):
+        seed = workloads.seed_for(5, t) if seed0 is None else seed0 + t
+        wl = workloads.drum(n=n_particles, seed=seed, omega=omega, precision="mixed", spacing=0.999)
+        g = DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="mixed", device=dev)
+        r = torch.tensor(wl.radius, device=dev)
+        geom = drum_geometry(wl, dev)
+        cut = 1.2 * 2.0 * float(wl.radius.max())
+        g.step(settle_steps)
+        for _ in range(samples_per_traj):
+            x0, v0, w0 = _state(g, wl.n, dev)
+            g.step(K_STEPS)
+            _, v1, w1 = _state(g, wl.n, dev)
+            G = Graph(x0, cut, wl.cfg["domain_lo"], wl.cfg["domain_hi"])
+            X, E = net.features(x0, v0, w0, r, G, geom)
+            T = torch.empty((wl.n, 6), dtype=torch.float32, device=dev)
+            _ok("surr_targets", lib().surr_targets(_p(v0), _p(w0), _p(v1), _p(w1), _p(r), wl.n, _p(geom),
+                                                   _p(net.out_scale), _p(T), _stream(torch, dev)))
+            out.append(Sample(G, X, E, T))
+            g.step(gap_steps)
+        g.close()
+    return out
+
+
+def fit_output_scale(net, samples):
+    """Per-output scale = RMS of the (unscaled) targets, so every output has unit size."""
+    import torch
+    T = torch.cat([s.T for s in samples]) * net.out_scale
+    sc = torch.sqrt((T.double() ** 2).mean(0)).float().clamp_min(1e-12)
+    for s in samples:
+        s.T.mul_(net.out_scale / sc)
+    net.out_scale = sc
+
+
+def train(net, samples, epochs, lr=1e-3, seed=0):
+    import torch
+    w = torch.ones(6, dtype=torch.float32, device=net.dev)
+    rng = np.random.default_rng(seed)
+    hist = []
+    for ep in range(epochs):
+        tot = torch.zeros(1, dtype=torch.float32, device=net.dev)
+        for k in rng.permutation(len(samples)):
+            s = samples[k]
+            tot += net.train_step(s.X, s.E, s.graph, s.T, w, lr)
+        hist.append(float(tot.item()) / len(samples))
+    return hist
+
+
+def evaluate(net, samples):
+    """(MSE of the network, MSE of predicting no change) over samples, scaled targets."""
+    import torch
+    w = torch.ones(6, dtype=torch.float32, device=net.dev)
+    a = b = 0.0
+    for s in samples:
+        Y = net.forward(s.X, s.E, s.graph)
+        loss, _ = net.loss_grad(Y, s.T, w)
+        a += float(loss.item())
+        b += float((s.T.double() ** 2).mean().item())
+    return a / len(samples), b / len(samples)
+
+
+def rollout(net, wl, dem_ctx, n_equiv_steps, max_overlap=0.05, max_ke_jump=0.5, device="cuda"):
+    """Advances the drum by n_equiv_steps DEM-step equivalents with the surrogate (K_STEPS
+    per network evaluation), starting from dem_ctx's current state.  Before each surrogate
+    step the state is checked: if the largest overlap exceeds max_overlap of the largest
+    diameter or the kinetic energy changed by more than max_ke_jump (relative) over the
+    last step, the K_STEPS are taken by plain DEM from the current state instead
+    (fallback).  Returns the final state, the number of fallbacks and of surrogate steps."""
+    import torch
+    dev = torch.device(device)
+    x, v, w = _state(dem_ctx, wl.n, dev)
+    r = torch.tensor(wl.radius, device=dev)
+    m = torch.tensor(wl.cfg["density"] * 4.0 / 3.0 * np.pi * wl.radius.astype(np.float64) ** 3, device=dev)
+    geom = drum_geometry(wl, dev)
+    d0 = 2.0 * float(wl.radius.max())
+    cut = 1.2 * d0
+    kdt = K_STEPS * wl.cfg["dt"]
+    ke_prev = None
+    fall = surr = 0
+    for _ in range(n_equiv_steps // K_STEPS):
+        G = Graph(x, cut, wl.cfg["domain_lo"], wl.cfg["domain_hi"])
+        X, E = net.features(x, v, w, r, G, geom)
+        ke = float((0.5 * m * (v * v).sum(1)).sum().item())
+        ovl = 0.01 * float(E[: G.n_edges, 4].max().item()) if G.n_edges else 0.0   # in d0
+        bad = ovl > max_overlap or (ke_prev is not None and abs(ke - ke_prev) > max_ke_jump * max(ke_prev, 1e-12))
+        if bad:
+            dem_ctx.set_state(x, v, w)
+            dem_ctx.step(K_STEPS)
+            x, v, w = _state(dem_ctx, wl.n, dev)
+            fall += 1
+            ke_prev = None
+            continue
+        Y = net.forward(X, E, G)
+        net.apply(x, v, w, r, Y, geom, kdt)
+        surr += 1
+        ke_prev = ke
+    return (x, v, w), fall, surr

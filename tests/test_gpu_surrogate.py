@@ -23,7 +23,8 @@ def test_bf16_tensor_core_product_matches_fp64():
         A = S.round_bf16(rng.normal(size=(M, K)))
         B = S.round_bf16(rng.normal(size=(K, N)))
         Ct = torch.empty((M, N), dtype=torch.float32, device="cuda")
-        code = SG.lib().surr_gemm_bf16(SG._p(bf16_array(A)), SG._p(bf16_array(B)), SG._p(Ct), M, K, N, None)
+        At, Bt = bf16_array(A), bf16_array(B)          # kept alive until the product is read
+        code = SG.lib().surr_gemm_bf16(SG._p(At), SG._p(Bt), SG._p(Ct), M, K, N, None)
         assert code == 0
         ref = A @ B
         err = np.abs(Ct.cpu().numpy() - ref).max() / np.abs(ref).max()

@@ -50,8 +50,8 @@ def test_sums_equal_dense_adjacency_products():
     recv = np.repeat(np.arange(n), np.diff(row_ptr))
     assert np.array_equal(np.sort(np.stack([recv, col], 1), axis=0), np.sort(np.argwhere(Adj > 0), axis=0))
     Y, c = S.forward(p, X, E, row_ptr, col, bf16=False)
-    assert np.allclose(c["s1"], Adj @ c["h1"], rtol=1e-13, atol=1e-13)
-    assert np.allclose(c["s2"], Adj @ c["h2"], rtol=1e-13, atol=1e-13)
+    assert np.allclose(c["s1"], S.AGG * (Adj @ c["h1"]), rtol=1e-13, atol=1e-13)
+    assert np.allclose(c["s2"], S.AGG * (Adj @ c["h2"]), rtol=1e-13, atol=1e-13)
 
 
 def test_bf16_rounding_is_nearest_even():

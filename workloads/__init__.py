@@ -196,15 +196,19 @@ def drum(n: int = 200_000, seed: int | None = None, rmin: float = 1.5e-3, rmax: 
     R = (solid / (0.3 * math.pi * aspect)) ** (1.0 / 3.0)
     if fill_scale is not None:
         R *= fill_scale
-    L = aspect * R
     dmax = 2.0 * rmax
     a = spacing * dmax
-    pts = _fcc(a, (-R, 0.0, -R), (R, L, R))
-    rho = np.hypot(pts[:, 0], pts[:, 2])
-    inside = (rho < R - 0.55 * dmax) & (pts[:, 1] > 0.55 * dmax) & (pts[:, 1] < L - 0.55 * dmax)
-    pts = pts[inside]
-    if len(pts) < n:
-        raise RuntimeError(f"drum lattice holds {len(pts)} < {n} spheres")
+    while True:
+        # small drums lose a larger share of lattice sites to the wall margins: grow the
+        # drum (by 1 % steps) only when the lattice would not hold all the spheres
+        L = aspect * R
+        pts = _fcc(a, (-R, 0.0, -R), (R, L, R))
+        rho = np.hypot(pts[:, 0], pts[:, 2])
+        inside = (rho < R - 0.55 * dmax) & (pts[:, 1] > 0.55 * dmax) & (pts[:, 1] < L - 0.55 * dmax)
+        pts = pts[inside]
+        if len(pts) >= n:
+            break
+        R *= 1.01
     pts = pts[np.argsort(pts[:, 2], kind="stable")][:n]     # lowest lattice sites first
     x = pts + rng.uniform(-0.01, 0.01, pts.shape) * dmax
     axis = (0.0, 1.0, 0.0)
