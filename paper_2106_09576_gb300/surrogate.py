@@ -277,13 +277,15 @@ def evaluate(net, samples):
     return a / len(samples), b / len(samples)
 
 
-def rollout(net, wl, dem_ctx, n_equiv_steps, max_overlap=0.05, max_ke_jump=0.5, device="cuda"):
+def rollout(net, wl, dem_ctx, n_equiv_steps, max_overlap=0.015, max_ke_gain=0.2, device="cuda"):
     """Advances the drum by n_equiv_steps DEM-step equivalents with the surrogate (K_STEPS
-    per network evaluation), starting from dem_ctx's current state.  Before each surrogate
-    step the state is checked: if the largest overlap exceeds max_overlap of the largest
-    diameter or the kinetic energy changed by more than max_ke_jump (relative) over the
-    last step, the K_STEPS are taken by plain DEM from the current state instead
-    (fallback).  Returns the final state, the number of fallbacks and of surrogate steps."""
+    per network evaluation), starting from dem_ctx's current state.  Each surrogate step is
+    checked on the state it produces: if the largest overlap exceeds max_overlap of the
+    largest diameter, or the kinetic energy (translation and spin) exceeds by more than
+    max_ke_gain the energy of the last state plain DEM produced (the start, or the last
+    fallback), the step is discarded and the K_STEPS are taken by plain DEM from the
+    previous state instead (fallback).  Returns the final state, the number of fallbacks
+    and of surrogate steps."""
     import torch
     dev = torch.device(device)
     x, v, w = _state(dem_ctx, wl.n, dev)
@@ -293,23 +295,34 @@ def rollout(net, wl, dem_ctx, n_equiv_steps, max_overlap=0.05, max_ke_jump=0.5, 
     d0 = 2.0 * float(wl.radius.max())
     cut = 1.2 * d0
     kdt = K_STEPS * wl.cfg["dt"]
-    ke_prev = None
+    lo, hi = wl.cfg["domain_lo"], wl.cfg["domain_hi"]
+
+    inertia = 0.4 * m * r.double() ** 2
+
+    def ke(v_, w_):
+        return float((0.5 * m * (v_ * v_).sum(1) + 0.5 * inertia * (w_ * w_).sum(1)).sum().item())
+
+    ke_ref = ke(v, w)
+
     fall = surr = 0
+    G = Graph(x, cut, lo, hi)
     for _ in range(n_equiv_steps // K_STEPS):
-        G = Graph(x, cut, wl.cfg["domain_lo"], wl.cfg["domain_hi"])
         X, E = net.features(x, v, w, r, G, geom)
-        ke = float((0.5 * m * (v * v).sum(1)).sum().item())
-        ovl = 0.01 * float(E[: G.n_edges, 4].max().item()) if G.n_edges else 0.0   # in d0
-        bad = ovl > max_overlap or (ke_prev is not None and abs(ke - ke_prev) > max_ke_jump * max(ke_prev, 1e-12))
-        if bad:
-            dem_ctx.set_state(x, v, w)
-            dem_ctx.step(K_STEPS)
-            x, v, w = _state(dem_ctx, wl.n, dev)
-            fall += 1
-            ke_prev = None
-            continue
         Y = net.forward(X, E, G)
-        net.apply(x, v, w, r, Y, geom, kdt)
-        surr += 1
-        ke_prev = ke
+        x1, v1, w1 = x.clone(), v.clone(), w.clone()
+        net.apply(x1, v1, w1, r, Y, geom, kdt)
+        G1 = Graph(x1, cut, lo, hi)
+        X1, E1 = net.features(x1, v1, w1, r, G1, geom)
+        ovl = 0.01 * float(E1[: G1.n_edges, 4].max().item()) if G1.n_edges else 0.0   # in d0
+        k1 = ke(v1, w1)
+        if ovl <= max_overlap and k1 == k1 and k1 <= ke_ref * (1.0 + max_ke_gain) + 1e-12:
+            x, v, w, G = x1, v1, w1, G1
+            surr += 1
+            continue
+        dem_ctx.set_state(x, v, w)
+        dem_ctx.step(K_STEPS)
+        x, v, w = _state(dem_ctx, wl.n, dev)
+        G = Graph(x, cut, lo, hi)
+        ke_ref = ke(v, w)
+        fall += 1
     return (x, v, w), fall, surr

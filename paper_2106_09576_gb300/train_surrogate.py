@@ -1,0 +1,95 @@
+"""Trains the drum surrogate on DEM trajectories and compares it with plain DEM.
+
+    python -m paper_2106_09576_gb300.train_surrogate [--trajectories 200] [--eval-steps 50000]
+
+1. 200 seeded DEM trajectories of small drums (the 200k drum's materials, radii and speed)
+   give (state, increments over 10 steps) samples; 10 more trajectories are held out.
+2. Training with the library's kernels (forward, backward, Adam).
+3. On held-out drums, from a settled state: plain DEM and the surrogate with DEM fallback
+   each advance the same number of DEM-step equivalents; the dynamic angle of repose and
+   the kinetic energy are compared, with the wall time per equivalent step of each.
+Prints one JSON object (and writes it to --out if given).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    import workloads
+    from . import surrogate as SG
+    from .dem import DEM
+    from .observables import angle_of_repose, kinetic_energy
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--trajectories", type=int, default=200)
+    ap.add_argument("--held-out", type=int, default=10)
+    ap.add_argument("--particles", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--eval-steps", type=int, default=50000)
+    ap.add_argument("--eval-drums", type=int, default=3)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    dev = torch.device("cuda")
+    t0 = time.perf_counter()
+    net = SG.SurrogateNet()
+    train = SG.drum_trajectories(a.trajectories, a.particles, 4000, 6, 60, net)
+    SG.fit_output_scale(net, train)
+    held = SG.drum_trajectories(a.held_out, a.particles, 4000, 6, 60, net, seed0=workloads.seed_for(5, 900))
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = SG.train(net, train, a.epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    mse, zero = SG.evaluate(net, held)
+
+    rows = []
+    for k in range(a.eval_drums):
+        wl = workloads.drum(n=a.particles, seed=workloads.seed_for(5, 950 + k), omega=1.0, precision="mixed",
+                            spacing=0.999)
+        L, dmax = wl.cfg["drum_length"], 2.0 * float(wl.radius.max())
+        res = {}
+        for mode in ("dem", "surrogate"):
+            g = DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="mixed", device=dev)
+            g.step(20000)                                   # settle and start tumbling
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            if mode == "dem":
+                g.step(a.eval_steps)
+                x, v, w, act = g.state()
+                fall = surr = 0
+            else:
+                (xt, vt, wt), fall, surr = SG.rollout(net, wl, g, a.eval_steps)
+                x, v, w = xt.cpu().numpy(), vt.cpu().numpy(), wt.cpu().numpy()
+                act = np.ones(wl.n, bool)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t
+            res[mode] = dict(seconds=dt, us_per_equiv_step=1e6 * dt / a.eval_steps,
+                             angle_deg=angle_of_repose(x, wl.radius, act, L, dmax),
+                             kinetic_energy=kinetic_energy(v, w, wl.radius, wl.cfg["density"], act),
+                             fallbacks=fall, surrogate_steps=surr)
+            g.close()
+        rows.append(res)
+    ang_err = [abs(r["surrogate"]["angle_deg"] - r["dem"]["angle_deg"]) for r in rows]
+    ke_err = [abs(r["surrogate"]["kinetic_energy"] - r["dem"]["kinetic_energy"]) / max(r["dem"]["kinetic_energy"],
+                                                                                       1e-30) for r in rows]
+    speed = [r["dem"]["seconds"] / r["surrogate"]["seconds"] for r in rows]
+    out = dict(trajectories=a.trajectories, samples=len(train), particles=a.particles, epochs=a.epochs,
+               seconds_data=t_data, seconds_train=t_train, loss_history=hist,
+               held_out_mse=mse, held_out_mse_no_change=zero, eval_equiv_steps=a.eval_steps, drums=rows,
+               angle_error_deg=ang_err, kinetic_energy_rel_error=ke_err, speed_vs_dem=speed)
+    txt = json.dumps(out)
+    print(txt)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(txt + "\n")
+
+
+if __name__ == "__main__":
+    main()
