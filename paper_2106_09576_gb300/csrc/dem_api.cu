@@ -182,6 +182,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
 __global__ void k_begin(Params P, cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_reb,
                         int in_graph) {
   Control* C = P.ctl;
+  apply_flip(C);   // the previous evaluation's parities
   const long long rem = C->remaining;
   C->last = rem <= 1 ? 1 : 0;
   C->remaining = rem - 1;
@@ -203,12 +204,14 @@ __global__ void k_begin(Params P, cudaGraphConditionalHandle h_loop, cudaGraphCo
   C->n_wall_touch = 0ull;
   C->n_active = 0ull;
   C->max_ovl_bits = 0u;
-  C->blocks_done = 0u;
   if (in_graph) {
     cudaGraphSetConditional(h_reb, (unsigned)need);
     cudaGraphSetConditional(h_loop, rem - 1 > 0 ? 1u : 0u);
   }
 }
+
+// Closes a dem_step call: applies the last evaluation's parity flip.
+__global__ void k_end(Params P) { apply_flip(P.ctl); }
 
 __global__ void k_set_remaining(Control* C, long long n_steps) {
   C->remaining = n_steps + (C->init ? 1 : 0);
@@ -535,7 +538,7 @@ void destroy_graph(dem_ctx* c) {
   c->exec = nullptr;
 }
 
-// WHILE(loop) { k_begin -> IF(rebuild) { rebuild } -> k_step }
+// WHILE(loop) { k_begin -> IF(rebuild) { rebuild } -> k_step } -> k_end
 dem_status build_graph(dem_ctx* c) {
   destroy_graph(c);
   cudaGraph_t g = nullptr;
@@ -582,6 +585,10 @@ dem_status build_graph(dem_ctx* c) {
       break;
     launch_step(c->P, cs);
     if (cudaStreamEndCapture(cs, &body) != cudaSuccess) break;
+    if (cudaStreamBeginCaptureToGraph(cs, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    k_end<<<1, 1, 0, cs>>>(c->P);
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess) break;
     if (cudaGraphInstantiate(&c->exec, g, 0) != cudaSuccess) {
       c->exec = nullptr;
       break;
@@ -616,6 +623,7 @@ dem_status run_eager(dem_ctx* c, long long n_steps) {
     if (need) launch_rebuild(c->P, c->stream);
     launch_step(c->P, c->stream);
   }
+  k_end<<<1, 1, 0, c->stream>>>(c->P);
   CK(cudaGetLastError());
   return DEM_OK;
 }
@@ -957,6 +965,7 @@ dem_status dem_step_profiled(dem_ctx* c, int64_t n_steps, double* step_kernel_ms
     }
     for (auto& ev : e) cudaEventDestroy(ev);
     if (st != DEM_OK) return st;
+    k_end<<<1, 1, 0, c->stream>>>(c->P);
     CK(cudaGetLastError());
   }
   if (step_kernel_ms) *step_kernel_ms = ks;

@@ -95,7 +95,7 @@ struct Control {
   int max_nbr_seen;
   unsigned wall_on;     // bit k: wall k exists at the time of the current evaluation
   int do_rebuild;       // decision of the current iteration (read by the host in eager mode)
-  unsigned blocks_done; // step-kernel blocks finished (the last one flips the parities)
+  int flip_due;         // 1: a step kernel ran; its parity flip is not applied yet
   unsigned status;      // sticky error bits
   unsigned max_ovl_bits;  // float bits of max delta_n / R over the last step
   long long step;       // completed time steps
@@ -108,6 +108,18 @@ struct Control {
   unsigned long long n_active;
   unsigned long long n_active_now;  // scratch of dem_get_stats
 };
+
+// Applies the parity flip a step kernel left due (see end_step): the state and history
+// parities, and the end of the initial evaluation.  One thread.
+__device__ __forceinline__ void apply_flip(Control* C) {
+  if (C->flip_due) {
+    C->cur ^= 1;
+    C->hc ^= 1;
+    C->init = 0;
+    C->ran = 1;
+    C->flip_due = 0;
+  }
+}
 
 struct Params {
   int n;

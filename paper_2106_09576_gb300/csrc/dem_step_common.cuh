@@ -318,23 +318,18 @@ __device__ __forceinline__ void block_flush(const StepStats& s, Control* C) {
   }
 }
 
-// The last block to finish flips the state and history parities and clears the
-// initial-evaluation flag: every block has read them by then.  No fence is needed before
-// the count: the last block writes only these control words, whose old values every
-// block consumed before counting itself, and the next kernel on the stream sees all of
-// this kernel's writes.
-__device__ __forceinline__ void finish_step(Control* C) {
-  __shared__ bool is_last;
-  if (threadIdx.x == 0) is_last = atomicAdd(&C->blocks_done, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (is_last && threadIdx.x == 0) {
-    C->cur ^= 1;
-    C->hc ^= 1;
-    C->init = 0;
-    C->ran = 1;
-    C->blocks_done = 0;
-    __threadfence();
-  }
+// End of an evaluation.  The counters of dem_get_stats describe the last evaluation of a
+// dem_step call, so only that one reduces them; the others publish error bits alone (rare,
+// one atomic per failing thread).  The parities of the state and the history flip after
+// the kernel: it only marks the flip as due (a plain store of one thread), and the next
+// k_begin or the k_end closing the call applies it (apply_flip), so no block waits on a
+// grid-wide count.
+__device__ __forceinline__ void end_step(const StepStats& st, Control* C, bool last) {
+  if (last)
+    block_flush(st, C);
+  else if (st.status)
+    atomicOr(&C->status, st.status);
+  if (blockIdx.x == 0 && threadIdx.x == 0) C->flip_due = 1;
 }
 
 // Exact "z < z_sink" on FP64 values with integer operations.

@@ -227,8 +227,7 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
     }
   }
   if (P.max_overlap_ratio > 0.0 && st.max_ovl > (float)P.max_overlap_ratio) st.status |= kStOverlap;
-  block_flush(st, P.ctl);
-  finish_step(P.ctl);
+  end_step(st, P.ctl, last);
 }
 
 void launch_step_fp64(const Params& P, cudaStream_t s) {

@@ -354,8 +354,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
     }
   }
   if (P.max_overlap_ratio > 0.0 && st.max_ovl > (float)P.max_overlap_ratio) st.status |= kStOverlap;
-  block_flush(st, P.ctl);
-  finish_step(P.ctl);
+  end_step(st, P.ctl, last);
 }
 
 void launch_step_mixed(const Params& P, cudaStream_t s) {
