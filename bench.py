@@ -194,24 +194,31 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _reduce(x, world, op):
+    """All-reduce of one number over the ranks (NCCL on the GPUs, gloo on CPU ranks)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+    return _reduce(x, world, dist.ReduceOp.MAX) if world > 1 else x
 
 
 def sum_over_ranks(x, world):
-    if world <= 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, world, dist.ReduceOp.SUM) if world > 1 else x
+
+
+def job_rate(units, ms, world):
+    """Whole-job throughput: the units every rank processed / the slowest rank's time."""
+    return sum_over_ranks(units, world) / (max_over_ranks(ms, world) / 1e3)
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -293,9 +300,10 @@ def run_batched(args, dev, world):
     g.step(args.batched_steps)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    ms_rank = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms_rank, world)
     st = g.stats()
-    value = sum_over_ranks(b.n * args.batched_steps, world) / (ms / 1e3)
+    value = job_rate(b.n * args.batched_steps, ms_rank, world)
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -365,8 +373,7 @@ def run_ours(args):
     st1 = g.stats()
     ms_max = max_over_ranks(ms, world)
     active = 0.5 * (st0["n_active"] + st1["n_active"])
-    psteps = sum_over_ranks(active * args.steps, world)
-    value = psteps / (ms_max / 1e3)
+    value = job_rate(active * args.steps, ms, world)
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
     launches = 1 + 2 * args.steps + REBUILD_KERNELS * rebuilds
 
