@@ -256,6 +256,10 @@ def oracle_rate(wl, seconds, max_steps=None, warmup=0):
     return s.n * steps / dt, s.n, steps, dt
 
 
+def sample_part(k, n):
+    return "all of it" if k >= n else "central column"
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -271,7 +275,7 @@ def run_reference(args):
         "data": "synthetic", "gpu_launches": 0,
         "config": {"workload": f"{desc}-{wl.n}", "sample": k, "parallelism": "single-thread CPU"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{k} spheres of the {desc} workload (central column), {steps} steps"},
+                         "sample": f"{k} spheres of the {desc} workload ({sample_part(k, wl.n)}), {steps} steps"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -375,7 +379,8 @@ def run_ours(args):
     active = 0.5 * (st0["n_active"] + st1["n_active"])
     value = job_rate(active * args.steps, ms, world)
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    launches = 1 + 2 * args.steps + REBUILD_KERNELS * rebuilds
+    # k_set_remaining and k_end per dem_step call, k_begin and the step kernel per step
+    launches = 2 + 2 * args.steps + REBUILD_KERNELS * rebuilds
 
     # ---------------- step-kernel roofline (CUDA events around each launch)
     kp = args.profile_steps if args.profile_steps is not None else min(args.steps, 200)
@@ -456,7 +461,7 @@ def run_ours(args):
     if not args.no_cpu and world == 1 and rank == 0:
         rate, k, steps, dt = oracle_rate(wl, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{k} spheres of the {desc} workload (central column), {steps} steps, "
+               "sample": f"{k} spheres of the {desc} workload ({sample_part(k, wl.n)}), {steps} steps, "
                          f"{dt:.1f} s, single thread, host CPU of the GPU box"}
 
     if rank == 0:
