@@ -94,9 +94,20 @@ int surr_targets(const double* v0, const double* w0, const double* v1, const dou
 int surr_apply(double* x, double* v, double* w, const float* radius, int64_t n, const float* Y, const double* geom,
                const float* out_scale, double kdt, void* stream);
 
-/* C[M][N] = A[M][K] B[K][N] with A, B BF16 row-major, C FP32: the tensor-core product used
- * by the network, exposed for its own test.  M any, K a multiple of 16, N a multiple of 8. */
+/* C[M][N] = A[M][K] B[K][N] with A, B BF16 row-major, C FP32: the warp-level tensor-core
+ * product (mma.sync) used by the backward pass and the decoder, exposed for its own test.
+ * M any, K a multiple of 16, N a multiple of 8. */
 int surr_gemm_bf16(const void* A, const void* B, float* C, int64_t M, int64_t K, int64_t N, void* stream);
+
+/* The same product for N = 128 on the 5th-generation tensor cores (tcgen05.mma, FP32
+ * accumulator in tensor memory), which the forward pass uses for its 128-wide layers:
+ * C [M][128] (FP32) = A [M][K] B [K][128] (BF16, row-major, 16-byte aligned rows); K a
+ * multiple of 16 from 16 to 256. */
+int surr_gemm_bf16_tc(const void* A, const void* B, float* C, int64_t M, int64_t K, void* stream);
+
+/* Waits on the tensor cores that ran out of their iteration limit since the library was
+ * loaded (synchronises the device; 0 in normal operation). */
+int surr_tc_timeouts(int* count);
 
 #ifdef __cplusplus
 }

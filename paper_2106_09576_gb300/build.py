@@ -27,6 +27,7 @@ SOURCES = {
     "dem_step_mixed.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "dem_static_pairs.cu": [],
     "surrogate.cu": [],
+    "surrogate_tc.cu": [],
 }
 
 

@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "../../include/surrogate.h"
+#include "surrogate_tc.cuh"
 
 namespace {
 
@@ -570,24 +571,24 @@ extern "C" int surr_forward(const void* params_bf16, const float* params, const 
   k_to_bf16<<<nblk(n * FIN, T), T, 0, s>>>(X, w.Xb, n * FIN);
   if (nE > 0) k_to_bf16<<<nblk(nE * EIN, T), T, 0, s>>>(E, w.Eb, nE * EIN);
   k_receivers<<<nblk(n, T), T, 0, s>>>(row_ptr, n, w.recv);
-  // node encoder
-  gemm(CatA{w.Xb, nullptr, FIN, nullptr, 0}, MatB{Pb + L.W[0], H, 0}, n, H, FIN, w.C, s);
-  k_epilogue<<<nblk(n * H, T), T, 0, s>>>(w.C, params + L.b[0], n, H, 1, nullptr, nullptr, w.h0, nullptr);
+  // node encoder and the 128-wide layers on the tensor cores (tcgen05), epilogues fused
+  const bf16* W = Pb;
+  auto tc = [&](const bf16* s0, const int32_t* g0, int w0, const bf16* s1, int w1, int l, const bf16* res,
+                bf16* u_out, bf16* out, int64_t M) {
+    surrtc::Args a{s0, g0, w0, s1, w1, W + L.W[l], params + L.b[l], 1, res, u_out, out, nullptr, M};
+    return surrtc::launch(a, s);
+  };
+  bool ok = tc(w.Xb, nullptr, FIN, nullptr, 0, 0, nullptr, nullptr, w.h0, n);
   // edge messages and their sum at each receiver
-  if (nE > 0) {
-    gemm(CatA{w.h0, w.recv, H, w.Eb, EIN}, MatB{Pb + L.W[1], H, 0}, nE, H, H + EIN, w.C, s);
-    k_epilogue<<<nblk(nE * H, T), T, 0, s>>>(w.C, params + L.b[1], nE, H, 1, nullptr, nullptr, w.u1, nullptr);
-  }
+  if (nE > 0) ok = ok && tc(w.h0, w.recv, H, w.Eb, EIN, 1, nullptr, nullptr, w.u1, nE);
   k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, nullptr, w.u1, nullptr, H, n, w.a, nullptr, 0, kAgg);
-  gemm(CatA{w.h0, nullptr, H, w.a, H}, MatB{Pb + L.W[2], H, 0}, n, H, 2 * H, w.C, s);
-  k_epilogue<<<nblk(n * H, T), T, 0, s>>>(w.C, params + L.b[2], n, H, 1, w.h0, w.u2, w.h1, nullptr);
+  ok = ok && tc(w.h0, nullptr, H, w.a, H, 2, w.h0, w.u2, w.h1, n);
   // two node layers on neighbour sums
   k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, w.h1, nullptr, H, n, w.s1, nullptr, 0, kAgg);
-  gemm(CatA{w.h1, nullptr, H, w.s1, H}, MatB{Pb + L.W[3], H, 0}, n, H, 2 * H, w.C, s);
-  k_epilogue<<<nblk(n * H, T), T, 0, s>>>(w.C, params + L.b[3], n, H, 1, w.h1, w.u3, w.h2, nullptr);
+  ok = ok && tc(w.h1, nullptr, H, w.s1, H, 3, w.h1, w.u3, w.h2, n);
   k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, w.h2, nullptr, H, n, w.s2, nullptr, 0, kAgg);
-  gemm(CatA{w.h2, nullptr, H, w.s2, H}, MatB{Pb + L.W[4], H, 0}, n, H, 2 * H, w.C, s);
-  k_epilogue<<<nblk(n * H, T), T, 0, s>>>(w.C, params + L.b[4], n, H, 1, w.h2, w.u4, w.h3, nullptr);
+  ok = ok && tc(w.h2, nullptr, H, w.s2, H, 4, w.h2, w.u4, w.h3, n);
+  if (!ok) return 2;
   // decoder
   gemm(CatA{w.h3, nullptr, H, nullptr, 0}, MatB{Pb + L.W[5], NOUT, 0}, n, NOUT, H, w.C, s);
   k_epilogue<<<nblk(n * NOUT, T), T, 0, s>>>(w.C, params + L.b[5], n, NOUT, 0, nullptr, nullptr, nullptr, Y);
@@ -675,6 +676,19 @@ extern "C" int surr_gemm_bf16(const void* A, const void* B, float* C, int64_t M,
   gemm(CatA{(const bf16*)A, nullptr, (int)K, nullptr, 0}, MatB{(const bf16*)B, (int)N, 0}, M, N, K, C,
        (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
+}
+
+extern "C" int surr_gemm_bf16_tc(const void* A, const void* B, float* C, int64_t M, int64_t K, void* stream) {
+  if (!A || !B || !C || M < 0 || K < 16 || K > 256 || K % 16) return 1;
+  surrtc::Args a{(const bf16*)A, nullptr, (int)K, nullptr, 0, (const bf16*)B, nullptr, 0, nullptr, nullptr, nullptr,
+                 C, M};
+  return surrtc::launch(a, (cudaStream_t)stream) ? 0 : 2;
+}
+
+extern "C" int surr_tc_timeouts(int* count) {
+  if (!count) return 1;
+  *count = surrtc::timeouts();
+  return *count < 0 ? 2 : 0;
 }
 
 extern "C" int surr_features(const double* x, const double* v, const double* w, const float* radius, int64_t n,

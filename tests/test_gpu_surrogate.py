@@ -31,6 +31,39 @@ def test_bf16_tensor_core_product_matches_fp64():
         assert err < 1e-5, (M, K, N, err)
 
 
+def test_tcgen05_product_matches_fp64():
+    """The 5th-generation tensor-core product (tcgen05.mma, accumulator in tensor memory)
+    the forward pass uses for its 128-wide layers: ragged row counts, every K the network
+    uses, one and several tiles per CTA."""
+    import ctypes
+    import torch
+    from paper_2106_09576_gb300 import surrogate as SG
+    rng = np.random.default_rng(3)
+    for (M, K) in [(1000, 144), (37, 16), (513, 256), (128, 128), (300, 64), (40000, 256)]:
+        A = S.round_bf16(rng.normal(size=(M, K)))
+        B = S.round_bf16(rng.normal(size=(K, 128)))
+        Ct = torch.full((M, 128), float("nan"), dtype=torch.float32, device="cuda")
+        At, Bt = bf16_array(A), bf16_array(B)          # kept alive until the product is read
+        assert SG.lib().surr_gemm_bf16_tc(SG._p(At), SG._p(Bt), SG._p(Ct), M, K, None) == 0
+        ref = A @ B
+        got = Ct.cpu().numpy()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < 1e-5, (M, K, err)
+    count = ctypes.c_int(-1)
+    assert SG.lib().surr_tc_timeouts(ctypes.byref(count)) == 0 and count.value == 0
+
+
+def test_tcgen05_rejects_shapes_outside_its_limits():
+    import torch
+    from paper_2106_09576_gb300 import surrogate as SG
+    A = torch.zeros((64, 272), dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros((272, 128), dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros((64, 128), dtype=torch.float32, device="cuda")
+    assert SG.lib().surr_gemm_bf16_tc(SG._p(A), SG._p(B), SG._p(C), 64, 272, None) == 1    # K > 256
+    assert SG.lib().surr_gemm_bf16_tc(SG._p(A), SG._p(B), SG._p(C), 64, 40, None) == 1     # K % 16
+    assert SG.lib().surr_gemm_bf16_tc(None, SG._p(B), SG._p(C), 64, 16, None) == 1
+
+
 def random_case(n=300, seed=1):
     rng = np.random.default_rng(seed)
     pts = rng.uniform(0, 1, (n, 3))
