@@ -5,8 +5,9 @@
 //
 // One CTA of 128 threads owns one 128 x 128 output tile at a time (persistent over tiles).
 // The weights (K x 128, at most 64 KB) are loaded once per CTA; the rows of A stream
-// through two 16 KB stages of 64 K-columns each with cp.async, so the copy of stage s + 1
-// overlaps the products of stage s.  A row of A may be gathered (the receiver's node state
+// through a ring of 2 to 4 stages of 64 K-columns (16 KB) with cp.async, continuing across
+// the CTA's tiles, so the copies of the next stages overlap the products and the epilogue
+// of the current one.  A row of A may be gathered (the receiver's node state
 // for an edge message), so A is copied per 16-byte chunk rather than as one tensor tile.
 // Products are issued by one thread; their completion is signalled on an mbarrier by
 // tcgen05.commit; every wait is bounded.
@@ -28,6 +29,7 @@ constexpr int kThreads = 128;
 constexpr int kStageBytes = TM * TK * 2;    // 16 KB
 constexpr int kMaxK = 256;
 constexpr int kMaxKStages = kMaxK / TK;
+constexpr int kMaxStages = 4;              // A stages in flight at most
 constexpr long long kSpinLimit = 1ll << 20;  // try_wait calls per wait (each may sleep)
 
 __device__ int g_timeouts;
@@ -61,6 +63,13 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// at most n groups of this thread's copies still in flight (n from 0 to kMaxStages - 1)
+__device__ __forceinline__ void cp_wait_dyn(int n) {
+  if (n <= 0) cp_wait<0>();
+  else if (n == 1) cp_wait<1>();
+  else if (n == 2) cp_wait<2>();
+  else cp_wait<3>();
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* b) {
@@ -163,16 +172,18 @@ __device__ __forceinline__ void epilogue32(const Args& a, int64_t row, int c0, f
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ Args a, int ns) {
   extern __shared__ uint8_t dyn[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t bar[kMaxStages];
   __shared__ uint32_t tmem_slot;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~(uintptr_t)1023);
-  uint8_t* As[2] = {base, base + kStageBytes};
-  uint8_t* Bs = base + 2 * kStageBytes;
+  uint8_t* Bs = base;                                   // nkb stages of W
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = a.w0 + a.w1, nkb = (K + TK - 1) / TK;
+  uint8_t* As = base + (size_t)nkb * kStageBytes;      // ns stages of A
   const int64_t tiles = (a.M + TM - 1) / TM;
+  const int64_t my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t Q = my_tiles * nkb;                    // stages this CTA streams
 
   if (warp == 0) {   // 128 columns of tensor memory: the 128 x 128 FP32 accumulator
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(&tmem_slot))
@@ -180,8 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bar[0]);
-    mbar_init(&bar[1]);
+    for (int b = 0; b < ns; b++) mbar_init(&bar[b]);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   // W (K x 128, N contiguous) into K-major stages: stage s, row n, chunk c holds
@@ -204,91 +214,90 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  int pend[2] = {0, 0};        // a commit on this buffer's barrier not waited for yet
-  uint32_t done[2] = {0u, 0u}; // commits waited for on this barrier (phase parity)
+  // Stage q of the stream is stage s = q % nkb of this CTA's tile q / nkb, in buffer q % ns.
+  // A buffer's barrier has at most one commit outstanding: it is waited for before the
+  // buffer is refilled, so a wait never confuses two phases of the same parity.
+  uint32_t pend = 0u;          // bit b: a commit on barrier b not waited for yet
+  uint32_t done = 0u;          // bit b: parity of the commits waited for on barrier b
   bool ok = true;
-  int64_t g = 0;               // stages issued by this CTA (buffer = g & 1)
   auto wait_buf = [&](int b) {
-    if (pend[b]) {
-      ok = mbar_wait(&bar[b], done[b] & 1u) && ok;
-      done[b]++;
-      pend[b] = 0;
+    if ((pend >> b) & 1u) {
+      ok = mbar_wait(&bar[b], (done >> b) & 1u) && ok;
+      done ^= 1u << b;
+      pend &= ~(1u << b);
+    }
+  };
+  // rows of tile `ti`, columns [64 s, 64 s + 64) of A into buffer `buf`; rows past M are
+  // zero, chunks past K are not read by any product and are left as they are
+  auto load = [&](int64_t q) {
+    const int64_t ti = blockIdx.x + (q / nkb) * gridDim.x;
+    const int s = (int)(q % nkb), buf = (int)(q % ns);
+    const int64_t m0 = ti * TM;
+    const int len = min(TK, K - s * TK);
+    const int c = tid & 7;
+    if (c * 8 >= len) return;
+    const int col = s * TK + c * 8;
+    const uint32_t dst0 = smem_u32(As + (size_t)buf * kStageBytes);
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int r = (tid >> 3) + 16 * j;
+      const int64_t m = m0 + r;
+      const bf16* src = a.s0;
+      int bytes = 0;
+      if (m < a.M) {
+        bytes = 16;
+        if (col < a.w0) {
+          const int64_t row = a.g0 ? (int64_t)a.g0[m] : m;
+          src = a.s0 + row * a.w0 + col;
+        } else {
+          src = a.s1 + m * a.w1 + (col - a.w0);
+        }
+      }
+      cp16(dst0 + sw128(r, c), src, bytes);
     }
   };
 
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t m0 = tile * TM;
-    // rows m0 .. m0 + 127, columns [64 s, 64 s + 64) of A into buffer buf; rows past M are
-    // zero, chunks past K are not read by any product and are left as they are
-    auto load = [&](int s, int buf) {
-      const int len = min(TK, K - s * TK);
-      const int c = tid & 7;
-      if (c * 8 >= len) return;
-      const int col = s * TK + c * 8;
-      const uint32_t dst0 = smem_u32(As[buf]);
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        const int r = (tid >> 3) + 16 * j;
-        const int64_t m = m0 + r;
-        const bf16* src = a.s0;
-        int bytes = 0;
-        if (m < a.M) {
-          bytes = 16;
-          if (col < a.w0) {
-            const int64_t row = a.g0 ? (int64_t)a.g0[m] : m;
-            src = a.s0 + row * a.w0 + col;
-          } else {
-            src = a.s1 + m * a.w1 + (col - a.w0);
-          }
-        }
-        cp16(dst0 + sw128(r, c), src, bytes);
-      }
-    };
-    {
-      const int b0 = (int)(g & 1);
-      wait_buf(b0);
-      load(0, b0);
-      cp_commit();
-    }
-    for (int s = 0; s < nkb; s++) {
-      const int b = (int)((g + s) & 1);
-      if (s + 1 < nkb) {
-        wait_buf(b ^ 1);      // the products that read the other buffer are done
-        load(s + 1, b ^ 1);
-        cp_commit();
-        cp_wait<1>();
-      } else {
-        cp_wait<0>();
-      }
-      fence_async_smem();     // this thread's copies are visible to the tensor cores
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const int len = min(TK, K - s * TK);
-        const uint64_t ad = desc_sw128(smem_u32(As[b]));
-        const uint64_t bd = desc_sw128(smem_u32(Bs + (size_t)s * kStageBytes));
-        for (int kk = 0; kk < len / 16; kk++)
-          mma_bf16(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (s > 0 || kk > 0) ? 1u : 0u);
-        mma_commit(&bar[b]);
-      }
-      pend[b] = 1;
-    }
-    g += nkb;
-    // all products of the tile are done when the last two commits are
-    const int bl = (int)((g - 1) & 1);
-    wait_buf(bl ^ 1);
-    wait_buf(bl);
-    tc_fence_after();
-    const int64_t row = m0 + warp * 32 + lane;
-#pragma unroll 1
-    for (int c0 = 0; c0 < TN; c0 += 32) {
-      float z[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, z);
-      if (ok && row < a.M) epilogue32(a, row, c0, z);
-    }
-    tc_fence_before();
-    __syncthreads();          // the accumulator is read before the next tile overwrites it
+  for (int64_t q = 0; q < ns - 1; q++) {   // the first ns - 1 stages in flight
+    if (q < Q) load(q);
+    cp_commit();
   }
+  for (int64_t q = 0; q < Q; q++) {
+    const int s = (int)(q % nkb), b = (int)(q % ns);
+    const int64_t qn = q + ns - 1;
+    if (qn < Q) {
+      wait_buf((int)(qn % ns));  // the products that read this buffer (stage q - 1) are done
+      load(qn);
+    }
+    cp_commit();
+    cp_wait_dyn(ns - 1);       // this thread's copies of stage q have landed
+    fence_async_smem();        // ... and are visible to the tensor cores
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const int len = min(TK, K - s * TK);
+      const uint64_t ad = desc_sw128(smem_u32(As + (size_t)b * kStageBytes));
+      const uint64_t bd = desc_sw128(smem_u32(Bs + (size_t)s * kStageBytes));
+      for (int kk = 0; kk < len / 16; kk++)
+        mma_bf16(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (s > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&bar[b]);
+    }
+    pend |= 1u << b;
+    if (s == nkb - 1) {        // the tile's products are done when its last commit is
+      wait_buf(b);
+      tc_fence_after();
+      const int64_t row = (blockIdx.x + (q / nkb) * gridDim.x) * TM + warp * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        float z[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, z);
+        if (ok && row < a.M) epilogue32(a, row, c0, z);
+      }
+      tc_fence_before();
+      __syncthreads();         // the accumulator is read before the next tile overwrites it
+    }
+  }
+  cp_wait_dyn(0);
+  for (int b = 0; b < ns; b++) wait_buf(b);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -319,18 +328,22 @@ bool launch(const Args& a, cudaStream_t s) {
     return false;
   if (a.M == 0) return true;
   const int nkb = (K + TK - 1) / TK;
-  const size_t smem = 1024 + (size_t)(2 + nkb) * kStageBytes;
+  // as many A stages (2 to 4) as leave room for two CTAs per SM next to the resident W
+  const size_t per_sm = 227 * 1024;
+  int ns = kMaxStages;
+  while (ns > 2 && 2 * (1024 + (size_t)(nkb + ns) * kStageBytes + 1024 + 64) > per_sm) ns--;
+  const size_t smem = 1024 + (size_t)(nkb + ns) * kStageBytes;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             1024 + (2 + kMaxKStages) * kStageBytes) != cudaSuccess)
+                             1024 + (kMaxKStages + kMaxStages) * kStageBytes) != cudaSuccess)
       return false;
     attr = true;
   }
   const int64_t tiles = (a.M + TM - 1) / TM;
   const int64_t cap = 2 * (int64_t)sm_count();
   const int grid = (int)(tiles < cap ? tiles : cap);
-  k_gemm_tc<<<grid, kThreads, smem, s>>>(a);
+  k_gemm_tc<<<grid, kThreads, smem, s>>>(a, ns);
   return cudaGetLastError() == cudaSuccess;
 }
 
