@@ -171,6 +171,32 @@ __global__ void k_epilogue(const float* C, const float* bias, int64_t M, int N, 
   if (outf) outf[e] = o;
 }
 
+// Y = h W5 + b5 for the 8 outputs: one thread per row, W5 (128 x 8) in shared memory, FP32
+// accumulation.  Eight columns are too narrow for a tensor-core tile.
+__global__ void __launch_bounds__(128) k_decoder(const bf16* h, const bf16* W, const float* b, int64_t n, float* Y) {
+  __shared__ float Ws[H * NOUT];
+  for (int e = threadIdx.x; e < H * NOUT; e += blockDim.x) Ws[e] = __bfloat162float(W[e]);
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float acc[NOUT];
+  for (int o = 0; o < NOUT; o++) acc[o] = b[o];
+  const uint4* hr = reinterpret_cast<const uint4*>(h + i * H);
+  for (int q = 0; q < H / 8; q++) {
+    const uint4 u = hr[q];
+    const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+    for (int p2 = 0; p2 < 4; p2++) {
+      const int k = 8 * q + 2 * p2;
+      const float x0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w4[p2] & 0xFFFFu)));
+      const float x1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w4[p2] >> 16)));
+      for (int o = 0; o < NOUT; o++) acc[o] = fmaf(x1, Ws[(k + 1) * NOUT + o], fmaf(x0, Ws[k * NOUT + o], acc[o]));
+    }
+  }
+  float4* yo = reinterpret_cast<float4*>(Y + i * NOUT);
+  yo[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+  yo[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+}
+
 __global__ void k_to_bf16(const float* src, bf16* dst, int64_t count) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < count) dst[e] = __float2bfloat16(src[e]);
@@ -590,8 +616,7 @@ extern "C" int surr_forward(const void* params_bf16, const float* params, const 
   ok = ok && tc(w.h2, nullptr, H, w.s2, H, 4, w.h2, w.u4, w.h3, n);
   if (!ok) return 2;
   // decoder
-  gemm(CatA{w.h3, nullptr, H, nullptr, 0}, MatB{Pb + L.W[5], NOUT, 0}, n, NOUT, H, w.C, s);
-  k_epilogue<<<nblk(n * NOUT, T), T, 0, s>>>(w.C, params + L.b[5], n, NOUT, 0, nullptr, nullptr, nullptr, Y);
+  k_decoder<<<nblk(n, 128), 128, 0, s>>>(w.h3, Pb + L.W[5], params + L.b[5], n, Y);
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

@@ -3,14 +3,15 @@
 // shared memory in the 128-byte-swizzled K-major layout, accumulators read back with
 // tcgen05.ld into a fused epilogue (bias, ReLU, residual, BF16 stores).
 //
-// One CTA of 128 threads owns one 128 x 128 output tile at a time (persistent over tiles).
+// A CTA of 160 threads works through 128 x 128 output tiles (persistent over tiles).
 // The weights (K x 128, at most 64 KB) are loaded once per CTA; the rows of A stream
 // through a ring of 2 to 4 stages of 64 K-columns (16 KB) with cp.async, continuing across
 // the CTA's tiles, so the copies of the next stages overlap the products and the epilogue
 // of the current one.  A row of A may be gathered (the receiver's node state
 // for an edge message), so A is copied per 16-byte chunk rather than as one tensor tile.
-// Products are issued by one thread; their completion is signalled on an mbarrier by
-// tcgen05.commit; every wait is bounded.
+// Four warps copy and run the epilogue, one thread of a fifth warp issues the products;
+// they hand stages and accumulators to each other through mbarriers (see k_gemm_tc); every
+// wait is bounded.
 //
 // Layers this narrow (N = 128) are bound by HBM, not by the tensor cores: a row of A of
 // K BF16 values feeds 256 K flops, i.e. 64 to 128 flops per byte moved, below the ~330
@@ -30,7 +31,7 @@ constexpr int kStageBytes = TM * TK * 2;    // 16 KB
 constexpr int kMaxK = 256;
 constexpr int kMaxKStages = kMaxK / TK;
 constexpr int kMaxStages = 4;              // A stages in flight at most
-constexpr long long kSpinLimit = 1ll << 20;  // try_wait calls per wait (each may sleep)
+constexpr long long kSpinLimit = 1ll << 18;  // try_wait calls per wait (each may sleep)
 
 __device__ int g_timeouts;
 
@@ -59,21 +60,10 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src, int bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// at most n groups of this thread's copies still in flight (n from 0 to kMaxStages - 1)
-__device__ __forceinline__ void cp_wait_dyn(int n) {
-  if (n <= 0) cp_wait<0>();
-  else if (n == 1) cp_wait<1>();
-  else if (n == 2) cp_wait<2>();
-  else cp_wait<3>();
-}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-__device__ __forceinline__ void mbar_init(uint64_t* b) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(b)) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
@@ -84,10 +74,14 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of the given parity; gives up after kSpinLimit attempts.
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  for (long long it = 0; it < kSpinLimit; it++)
+// Waits for the phase of the given parity; gives up after kSpinLimit attempts, or at once
+// when another thread of the CTA has given up (so a broken pipeline unwinds quickly).
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < kSpinLimit; it++) {
     if (mbar_try(b, parity)) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
   atomicAdd(&g_timeouts, 1);
   return false;
 }
@@ -172,10 +166,21 @@ __device__ __forceinline__ void epilogue32(const Args& a, int64_t row, int c0, f
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__ Args a, int ns) {
+// Roles: warps 0-3 (128 threads) copy A into the stage ring and run the epilogue (warp w
+// reads tensor-memory lanes 32 w .. 32 w + 31, i.e. rows 32 w .. of the tile); lane 0 of
+// warp 4 issues the products.  Barriers (parities follow the use count of each):
+//   full[b]      128 arrivals: every copier's copies of the stage in buffer b have landed
+//                (cp.async.mbarrier.arrive.noinc, no thread blocks on its own copies)
+//   empty[b]     tcgen05.commit after the products that read buffer b
+//   acc_full[a]  tcgen05.commit after the last products of a tile into accumulator a
+//   acc_empty[a] 128 arrivals: the epilogue has read accumulator a
+// Two accumulators (256 tensor-memory columns) let the products of tile t + 1 run during
+// the epilogue of tile t.
+__global__ void __launch_bounds__(kThreads + 32, 1) k_gemm_tc(const __grid_constant__ Args a, int ns) {
   extern __shared__ uint8_t dyn[];
-  __shared__ uint64_t bar[kMaxStages];
+  __shared__ uint64_t full[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dyn) + 1023) & ~(uintptr_t)1023);
   uint8_t* Bs = base;                                   // nkb stages of W
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -185,18 +190,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   const int64_t my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int64_t Q = my_tiles * nkb;                    // stages this CTA streams
 
-  if (warp == 0) {   // 128 columns of tensor memory: the 128 x 128 FP32 accumulator
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(&tmem_slot))
+  if (warp == 0) {   // 256 columns of tensor memory: two 128 x 128 FP32 accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(smem_u32(&tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    for (int b = 0; b < ns; b++) mbar_init(&bar[b]);
+    for (int b = 0; b < ns; b++) {
+      mbar_init(&full[b], kThreads);
+      mbar_init(&empty[b], 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], kThreads);
+    }
+    abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   // W (K x 128, N contiguous) into K-major stages: stage s, row n, chunk c holds
   // W[64 s + 8 c .. + 7][n]; columns past K are zero.
-  for (int it = tid; it < nkb * TN * 8; it += kThreads) {
+  for (int it = tid; it < nkb * TN * 8; it += blockDim.x) {
     const int s = it / (TN * 8), rem = it - s * (TN * 8), nr = rem >> 3, c = rem & 7;
     uint32_t w4[4];
 #pragma unroll
@@ -213,96 +226,124 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(const __grid_constant__
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  volatile int* abort = &abort_flag;
 
-  // Stage q of the stream is stage s = q % nkb of this CTA's tile q / nkb, in buffer q % ns.
-  // A buffer's barrier has at most one commit outstanding: it is waited for before the
-  // buffer is refilled, so a wait never confuses two phases of the same parity.
-  uint32_t pend = 0u;          // bit b: a commit on barrier b not waited for yet
-  uint32_t done = 0u;          // bit b: parity of the commits waited for on barrier b
-  bool ok = true;
-  auto wait_buf = [&](int b) {
-    if ((pend >> b) & 1u) {
-      ok = mbar_wait(&bar[b], (done >> b) & 1u) && ok;
-      done ^= 1u << b;
-      pend &= ~(1u << b);
-    }
-  };
-  // rows of tile `ti`, columns [64 s, 64 s + 64) of A into buffer `buf`; rows past M are
-  // zero, chunks past K are not read by any product and are left as they are
-  auto load = [&](int64_t q) {
-    const int64_t ti = blockIdx.x + (q / nkb) * gridDim.x;
-    const int s = (int)(q % nkb), buf = (int)(q % ns);
-    const int64_t m0 = ti * TM;
-    const int len = min(TK, K - s * TK);
-    const int c = tid & 7;
-    if (c * 8 >= len) return;
-    const int col = s * TK + c * 8;
-    const uint32_t dst0 = smem_u32(As + (size_t)buf * kStageBytes);
+  if (warp < 4) {
+    // ---------------- copiers and epilogue
+    bool ok = true;
+    // gathered rows: the source rows of this thread's 8 rows of the tile being copied
+    // (gidx), and those of the CTA's next tile, fetched while the current one is copied
+    // (pidx), so that no copy waits on a dependent index load
+    int gidx[8], pidx[8];
+    int64_t gtile = -1, ptile = -1;
+    auto fetch_idx = [&](int64_t t, int* dst) {
+      const int64_t m0 = (blockIdx.x + t * gridDim.x) * TM;
 #pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int r = (tid >> 3) + 16 * j;
-      const int64_t m = m0 + r;
-      const bf16* src = a.s0;
-      int bytes = 0;
-      if (m < a.M) {
-        bytes = 16;
-        if (col < a.w0) {
-          const int64_t row = a.g0 ? (int64_t)a.g0[m] : m;
-          src = a.s0 + row * a.w0 + col;
+      for (int j = 0; j < 8; j++) {
+        const int64_t m = m0 + (tid >> 3) + 16 * j;
+        dst[j] = m < a.M ? a.g0[m] : 0;
+      }
+    };
+    // stage q (stage q % nkb of this CTA's tile q / nkb) into buffer q % ns, then an
+    // arrival on full[] once this thread's copies have landed
+    auto load = [&](int64_t q) {
+      const int64_t t = q / nkb;
+      const int64_t ti = blockIdx.x + t * gridDim.x;
+      const int s = (int)(q % nkb), buf = (int)(q % ns);
+      if (q >= ns) ok = mbar_wait(&empty[buf], (uint32_t)((q / ns - 1) & 1), abort) && ok;
+      const int64_t m0 = ti * TM;
+      const int len = min(TK, K - s * TK);
+      const int c = tid & 7;
+      if (a.g0 && gtile != t) {
+        if (ptile == t) {
+#pragma unroll
+          for (int j = 0; j < 8; j++) gidx[j] = pidx[j];
         } else {
-          src = a.s1 + m * a.w1 + (col - a.w0);
+          fetch_idx(t, gidx);
+        }
+        gtile = t;
+      }
+      if (c * 8 < len) {
+        const int col = s * TK + c * 8;
+        const uint32_t dst0 = smem_u32(As + (size_t)buf * kStageBytes);
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const int r = (tid >> 3) + 16 * j;
+          const int64_t m = m0 + r;
+          const bf16* src = a.s0;
+          int bytes = 0;
+          if (m < a.M) {
+            bytes = 16;
+            if (col < a.w0) {
+              const int64_t row = a.g0 ? (int64_t)gidx[j] : m;
+              src = a.s0 + row * a.w0 + col;
+            } else {
+              src = a.s1 + m * a.w1 + (col - a.w0);
+            }
+          }
+          cp16(dst0 + sw128(r, c), src, bytes);
         }
       }
-      cp16(dst0 + sw128(r, c), src, bytes);
-    }
-  };
-
-  for (int64_t q = 0; q < ns - 1; q++) {   // the first ns - 1 stages in flight
-    if (q < Q) load(q);
-    cp_commit();
-  }
-  for (int64_t q = 0; q < Q; q++) {
-    const int s = (int)(q % nkb), b = (int)(q % ns);
-    const int64_t qn = q + ns - 1;
-    if (qn < Q) {
-      wait_buf((int)(qn % ns));  // the products that read this buffer (stage q - 1) are done
-      load(qn);
-    }
-    cp_commit();
-    cp_wait_dyn(ns - 1);       // this thread's copies of stage q have landed
-    fence_async_smem();        // ... and are visible to the tensor cores
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const int len = min(TK, K - s * TK);
-      const uint64_t ad = desc_sw128(smem_u32(As + (size_t)b * kStageBytes));
-      const uint64_t bd = desc_sw128(smem_u32(Bs + (size_t)s * kStageBytes));
-      for (int kk = 0; kk < len / 16; kk++)
-        mma_bf16(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), (s > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(&bar[b]);
-    }
-    pend |= 1u << b;
-    if (s == nkb - 1) {        // the tile's products are done when its last commit is
-      wait_buf(b);
-      tc_fence_after();
-      const int64_t row = (blockIdx.x + (q / nkb) * gridDim.x) * TM + warp * 32 + lane;
-#pragma unroll 1
-      for (int c0 = 0; c0 < TN; c0 += 32) {
-        float z[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, z);
-        if (ok && row < a.M) epilogue32(a, row, c0, z);
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full[buf])) : "memory");
+      if (a.g0 && s == 0 && ptile != t + 1 && t + 1 < my_tiles) {
+        fetch_idx(t + 1, pidx);
+        ptile = t + 1;
       }
-      tc_fence_before();
-      __syncthreads();         // the accumulator is read before the next tile overwrites it
+    };
+    for (int64_t q = 0; q < ns - 1 && q < Q; q++) load(q);
+    for (int64_t q = 0; q < Q; q++) {
+      if (q + ns - 1 < Q) load(q + ns - 1);
+      if ((int)(q % nkb) == nkb - 1) {   // epilogue of the tile that stage q ends
+        const int64_t t = q / nkb;
+        const int acc = (int)(t & 1);
+        ok = mbar_wait(&acc_full[acc], (uint32_t)((t >> 1) & 1), abort) && ok;
+        tc_fence_after();
+        const int64_t row = (blockIdx.x + t * gridDim.x) * TM + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TN; c0 += 32) {
+          float z[32];
+          tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * TN + c0), z);
+          if (ok && row < a.M) epilogue32(a, row, c0, z);
+        }
+        tc_fence_before();
+        asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(
+                         smem_u32(&acc_empty[acc]))
+                     : "memory");
+      }
+    }
+    cp_wait_all();
+  } else {
+    // ---------------- the issuer of the products: the whole warp waits, lane 0 issues
+    for (int64_t t = 0; t < my_tiles; t++) {
+      const int acc = (int)(t & 1);
+      if (t >= 2) mbar_wait(&acc_empty[acc], (uint32_t)(((t >> 1) - 1) & 1), abort);
+      tc_fence_after();
+      for (int s = 0; s < nkb; s++) {
+        const int64_t q = t * nkb + s;
+        const int b = (int)(q % ns);
+        mbar_wait(&full[b], (uint32_t)((q / ns) & 1), abort);
+        fence_async_smem();   // the copiers' writes, acquired through full[b], to the tensor cores
+        tc_fence_after();
+        if (lane == 0) {
+          const int len = min(TK, K - s * TK);
+          const uint64_t ad = desc_sw128(smem_u32(As + (size_t)b * kStageBytes));
+          const uint64_t bd = desc_sw128(smem_u32(Bs + (size_t)s * kStageBytes));
+          for (int kk = 0; kk < len / 16; kk++)
+            mma_bf16(tmem + (uint32_t)(acc * TN), ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk),
+                     (s > 0 || kk > 0) ? 1u : 0u);
+          mma_commit(&empty[b]);
+        }
+        __syncwarp();
+      }
+      if (lane == 0) mma_commit(&acc_full[acc]);
+      __syncwarp();
     }
   }
-  cp_wait_dyn(0);
-  for (int b = 0; b < ns; b++) wait_buf(b);
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem) : "memory");
   }
 }
 
@@ -332,7 +373,9 @@ bool launch(const Args& a, cudaStream_t s) {
   const size_t per_sm = 227 * 1024;
   int ns = kMaxStages;
   while (ns > 2 && 2 * (1024 + (size_t)(nkb + ns) * kStageBytes + 1024 + 64) > per_sm) ns--;
-  const size_t smem = 1024 + (size_t)(nkb + ns) * kStageBytes;
+  // at least 80 KB, so that no more than two CTAs (512 columns of tensor memory) share an SM
+  size_t smem = 1024 + (size_t)(nkb + ns) * kStageBytes;
+  if (smem < 80 * 1024) smem = 80 * 1024;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -343,7 +386,7 @@ bool launch(const Args& a, cudaStream_t s) {
   const int64_t tiles = (a.M + TM - 1) / TM;
   const int64_t cap = 2 * (int64_t)sm_count();
   const int grid = (int)(tiles < cap ? tiles : cap);
-  k_gemm_tc<<<grid, kThreads, smem, s>>>(a, ns);
+  k_gemm_tc<<<grid, kThreads + 32, smem, s>>>(a, ns);
   return cudaGetLastError() == cudaSuccess;
 }
 
