@@ -53,8 +53,9 @@ int surr_build_csr(const int32_t* pairs, int64_t n_pairs, int64_t n, int32_t* ro
 /* Converts the FP32 parameters to the BF16 copy. */
 int surr_params_to_bf16(const float* params, void* params_bf16, int64_t count, void* stream);
 
-/* Forward pass: X [n][16], E [n_edges][16] (FP32), Y [n][8] (FP32).  The workspace keeps
- * the activations the backward pass needs. */
+/* Forward pass: X [n][16], E [n_edges][16] (FP32), Y [n][8] (FP32), each 16-byte aligned.
+ * The 128-wide layers run on the 5th-generation tensor cores (see surr_gemm_bf16_tc).  The
+ * workspace keeps the activations the backward pass needs. */
 int surr_forward(const void* params_bf16, const float* params, const float* X, const float* E,
                  const int32_t* row_ptr, const int32_t* col, int64_t n, int64_t n_edges, void* workspace,
                  float* Y, void* stream);
