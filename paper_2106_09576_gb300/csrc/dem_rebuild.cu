@@ -247,7 +247,18 @@ __global__ void k_mirror_inactive(Params P) {
 }
 
 // ------------------------------------------------------------------ 4. fine search
-__global__ void k_neighbors(Params P) {
+// The list under construction (partner indices and their ids) lives in shared memory, one
+// row per thread (odd row stride: no bank conflicts between rows), so keeping it ordered by
+// partner id compares against ids already at hand instead of reloading them from global
+// memory; the finished row is copied out once.
+constexpr int kNbrBlock = 64;
+constexpr int kNbrRow = kMaxNbr + 1;
+
+__global__ void __launch_bounds__(kNbrBlock) k_neighbors(Params P) {
+  __shared__ int s_idx[kNbrBlock * kNbrRow];
+  __shared__ int s_id[kNbrBlock * kNbrRow];
+  int* ri = s_idx + threadIdx.x * kNbrRow;
+  int* rd = s_id + threadIdx.x * kNbrRow;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = P.n;
   const int nact = P.cell_start[P.n_cells];
@@ -301,11 +312,13 @@ __global__ void k_neighbors(Params P) {
               // insertion by partner id keeps the list ordered as a serial pair loop
               const int idj = ids[j];
               int k = cnt - 1;
-              while (k >= 0 && ids[out[k]] > idj) {
-                out[k + 1] = out[k];
+              while (k >= 0 && rd[k] > idj) {
+                ri[k + 1] = ri[k];
+                rd[k + 1] = rd[k];
                 k--;
               }
-              out[k + 1] = j;
+              ri[k + 1] = j;
+              rd[k + 1] = idj;
               cnt++;
             } else {
               overflow = true;
@@ -315,10 +328,17 @@ __global__ void k_neighbors(Params P) {
       }
     }
   }
+  for (int k = 0; k < cnt; k++) out[k] = ri[k];
   P.nbr_cnt[q] = cnt;
   if (overflow) atomicOr(&P.ctl->status, kStCapacity);
-  atomicMax(&P.ctl->max_nbr_seen, cnt + (overflow ? 1 : 0));
-  atomicAdd(&P.ctl->n_pairs_dir, (unsigned long long)cnt);
+  // one atomic per warp for the search statistics (not two per particle on two words)
+  const unsigned act = __activemask();
+  const unsigned wmax = __reduce_max_sync(act, (unsigned)(cnt + (overflow ? 1 : 0)));
+  const unsigned wsum = __reduce_add_sync(act, (unsigned)cnt);
+  if ((threadIdx.x & 31) == __ffs(act) - 1) {
+    atomicMax(&P.ctl->max_nbr_seen, (int)wmax);
+    atomicAdd(&P.ctl->n_pairs_dir, (unsigned long long)wsum);
+  }
 }
 
 // ------------------------------------------------------------------ 5. restore history
@@ -445,7 +465,7 @@ void launch_rebuild(const Params& P, cudaStream_t s) {
   k_permute<<<nb, T, 0, s>>>(P);
   k_mirror_inactive<<<nb, T, 0, s>>>(P);
   // 4. fine search
-  k_neighbors<<<nb, T, 0, s>>>(P);
+  k_neighbors<<<(P.n + kNbrBlock - 1) / kNbrBlock, kNbrBlock, 0, s>>>(P);
   // 5. history
   k_hist_load<<<nb, T, 0, s>>>(P);
   k_rebuild_end<<<1, 1, 0, s>>>(P);
