@@ -123,6 +123,36 @@ def test_forward_and_gradients_match_the_reference():
             assert e < 3e-2, (l, name, e)
 
 
+def test_forward_matches_the_reference_when_ctas_take_several_tiles():
+    """12,000 nodes and ~120,000 edges: the edge layer has ~940 tiles of 128 rows for 304
+    CTAs, so every CTA streams several tiles through its stage ring, alternates its two
+    tensor-memory accumulators and gathers receiver rows fetched a tile ahead."""
+    import torch
+    spatial = pytest.importorskip("scipy.spatial")
+    from paper_2106_09576_gb300 import surrogate as SG
+    rng = np.random.default_rng(11)
+    n = 12000
+    pts = rng.uniform(0, 1, (n, 3))
+    pairs = sorted(spatial.cKDTree(pts).query_pairs(0.0605))
+    row_ptr, col = S.csr(pairs, n)
+    assert len(col) > 3 * 304 * 128
+    X = rng.normal(size=(n, S.FIN))
+    E = rng.normal(size=(len(col), S.EIN))
+    _, total = S.layout()
+    p = (rng.normal(scale=0.06, size=total)).astype(np.float32).astype(np.float64)
+    g = gpu_graph(pairs, n, row_ptr, col)
+    net = SG.SurrogateNet()
+    net.params.copy_(torch.tensor(p, dtype=torch.float32))
+    net.sync_bf16()
+    Y = net.forward(torch.tensor(X, dtype=torch.float32, device="cuda"),
+                    torch.tensor(E, dtype=torch.float32, device="cuda"), g).cpu().numpy().astype(np.float64)
+    Yr, _ = S.forward(p, X, E, row_ptr, col, bf16=True)
+    rel = np.linalg.norm(Y - Yr) / np.linalg.norm(Yr)
+    worst = np.abs(Y - Yr).max() / np.abs(Yr).max()
+    print(f"forward relative error {rel:.2e}, worst element {worst:.2e}")
+    assert rel < 1e-2 and worst < 5e-2
+
+
 def test_training_reduces_the_loss_on_a_learnable_target():
     import torch
     from paper_2106_09576_gb300 import surrogate as SG
