@@ -209,11 +209,18 @@ def _state(dem_ctx, n, dev):
 
 
 def drum_trajectories(n_traj, n_particles, settle_steps, samples_per_traj, gap_steps, net, device="cuda",
-                      seed0=None, omega=1.0):
+                      seed0=None, omega=1.0, noise_v=0.0, noise_x=0.0):
     """Training samples from DEM runs of small rotating drums (the 200k drum's materials,
     radii and speed, scaled down; seeded per trajectory with seed_for(5, t)).  After
     settling, every gap_steps steps: the graph and features of a state and the increments
-    over the next K_STEPS steps.  Targets are scaled by net.out_scale."""
+    over the next K_STEPS steps.  Targets are scaled by net.out_scale.
+
+    With noise_v > 0 the input velocities and spins are perturbed by Gaussian noise of
+    standard deviation noise_v times the velocity scale (spins: divided by the radius), and
+    the targets become the increments from the perturbed state to the true one, so the
+    network learns to pull a drifting state back; noise_x perturbs the input positions by
+    noise_x times the largest diameter (the graph and the features see the perturbed
+    positions).  The noise is seeded per trajectory."""
     import torch
     import workloads
     from .dem import DEM
@@ -227,10 +234,19 @@ def drum_trajectories(n_traj, n_particles, settle_steps, samples_per_traj, gap_s
         geom = drum_geometry(wl, dev)
         cut = 1.2 * 2.0 * float(wl.radius.max())
         g.step(settle_steps)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        vs, d0 = float(geom[6]), float(geom[5])
         for _ in range(samples_per_traj):
             x0, v0, w0 = _state(g, wl.n, dev)
             g.step(K_STEPS)
             _, v1, w1 = _state(g, wl.n, dev)
+            if noise_v > 0.0:
+                v0 = v0 + noise_v * vs * torch.randn(v0.shape, generator=gen, device=dev, dtype=v0.dtype)
+                w0 = w0 + noise_v * vs * torch.randn(w0.shape, generator=gen, device=dev, dtype=w0.dtype) / \
+                    r.double()[:, None]
+            if noise_x > 0.0:
+                x0 = x0 + noise_x * d0 * torch.randn(x0.shape, generator=gen, device=dev, dtype=x0.dtype)
             G = Graph(x0, cut, wl.cfg["domain_lo"], wl.cfg["domain_hi"])
             X, E = net.features(x0, v0, w0, r, G, geom)
             T = torch.empty((wl.n, 6), dtype=torch.float32, device=dev)
@@ -279,15 +295,18 @@ def evaluate(net, samples):
     return a / len(samples), b / len(samples)
 
 
-def rollout(net, wl, dem_ctx, n_equiv_steps, max_overlap=0.015, max_ke_gain=0.2, device="cuda"):
+def rollout(net, wl, dem_ctx, n_equiv_steps, max_overlap=0.02, max_ke_gain=0.2, overlap_factor=0.0,
+            device="cuda", stats=None):
     """Advances the drum by n_equiv_steps DEM-step equivalents with the surrogate (K_STEPS
     per network evaluation), starting from dem_ctx's current state.  Each surrogate step is
-    checked on the state it produces: if the largest overlap exceeds max_overlap of the
-    largest diameter, or the kinetic energy (translation and spin) exceeds by more than
-    max_ke_gain the energy of the last state plain DEM produced (the start, or the last
-    fallback), the step is discarded and the K_STEPS are taken by plain DEM from the
-    previous state instead (fallback).  Returns the final state, the number of fallbacks
-    and of surrogate steps."""
+    checked on the state it produces: if the largest particle-particle overlap exceeds the
+    limit (max_overlap of the largest diameter, or overlap_factor times the largest overlap
+    of the last state plain DEM produced, whichever is larger), or the kinetic energy
+    (translation and spin) exceeds by more than max_ke_gain the energy of that DEM state
+    (the start, or the last fallback), the step is discarded and the K_STEPS are taken by
+    plain DEM from the previous state instead (fallback).  Returns the final state, the
+    number of fallbacks and of surrogate steps; `stats` (a dict), if given, receives the
+    rejections by cause and the mean largest overlap of the DEM states."""
     import torch
     dev = torch.device(device)
     x, v, w = _state(dem_ctx, wl.n, dev)
@@ -304,27 +323,42 @@ def rollout(net, wl, dem_ctx, n_equiv_steps, max_overlap=0.015, max_ke_gain=0.2,
     def ke(v_, w_):
         return float((0.5 * m * (v_ * v_).sum(1) + 0.5 * inertia * (w_ * w_).sum(1)).sum().item())
 
-    ke_ref = ke(v, w)
+    def largest_overlap(x_, v_, w_, G_):
+        if not G_.n_edges:
+            return 0.0
+        _, E_ = net.features(x_, v_, w_, r, G_, geom)
+        return 0.01 * float(E_[: G_.n_edges, 4].max().item())   # in d0
 
-    fall = surr = 0
+    fall = surr = rej_ovl = rej_ke = 0
     G = Graph(x, cut, lo, hi)
+    ke_ref = ke(v, w)
+    ovl_ref = largest_overlap(x, v, w, G)
+    ovl_sum, ovl_n = ovl_ref, 1
     for _ in range(n_equiv_steps // K_STEPS):
         X, E = net.features(x, v, w, r, G, geom)
         Y = net.forward(X, E, G)
         x1, v1, w1 = x.clone(), v.clone(), w.clone()
         net.apply(x1, v1, w1, r, Y, geom, kdt)
         G1 = Graph(x1, cut, lo, hi)
-        X1, E1 = net.features(x1, v1, w1, r, G1, geom)
-        ovl = 0.01 * float(E1[: G1.n_edges, 4].max().item()) if G1.n_edges else 0.0   # in d0
+        ovl = largest_overlap(x1, v1, w1, G1)
         k1 = ke(v1, w1)
-        if ovl <= max_overlap and k1 == k1 and k1 <= ke_ref * (1.0 + max_ke_gain) + 1e-12:
+        ovl_ok = ovl <= max(max_overlap, overlap_factor * ovl_ref)
+        ke_ok = k1 == k1 and k1 <= ke_ref * (1.0 + max_ke_gain) + 1e-12
+        if ovl_ok and ke_ok:
             x, v, w, G = x1, v1, w1, G1
             surr += 1
             continue
+        rej_ovl += 0 if ovl_ok else 1
+        rej_ke += 0 if ke_ok else 1
         dem_ctx.set_state(x, v, w)
         dem_ctx.step(K_STEPS)
         x, v, w = _state(dem_ctx, wl.n, dev)
         G = Graph(x, cut, lo, hi)
         ke_ref = ke(v, w)
+        ovl_ref = largest_overlap(x, v, w, G)
+        ovl_sum += ovl_ref
+        ovl_n += 1
         fall += 1
+    if stats is not None:
+        stats.update(rejected_overlap=rej_ovl, rejected_energy=rej_ke, dem_mean_largest_overlap=ovl_sum / ovl_n)
     return (x, v, w), fall, surr

@@ -3,11 +3,15 @@
     python -m paper_2106_09576_gb300.train_surrogate [--trajectories 200] [--eval-steps 50000]
 
 1. 200 seeded DEM trajectories of small drums (the 200k drum's materials, radii and speed)
-   give (state, increments over 10 steps) samples; 10 more trajectories are held out.
+   give (state, increments over 10 steps) samples, the input velocities and spins perturbed
+   by noise (0.1 of the velocity scale) so that the network learns to pull a drifting state
+   back; 10 more trajectories are held out (without noise).
 2. Training with the library's kernels (forward, backward, Adam).
 3. On held-out drums, from a settled state: plain DEM and the surrogate with DEM fallback
-   each advance the same number of DEM-step equivalents; the dynamic angle of repose and
-   the kinetic energy are compared, with the wall time per equivalent step of each.
+   (a surrogate step is rejected when the largest overlap exceeds 2 % of the diameter or
+   the kinetic energy grows by more than 20 %) each advance the same number of DEM-step
+   equivalents; the dynamic angle of repose and the kinetic energy are compared, with the
+   wall time per equivalent step of each.
 Prints one JSON object (and writes it to --out if given).
 """
 from __future__ import annotations
@@ -34,17 +38,24 @@ def main():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--eval-steps", type=int, default=50000)
     ap.add_argument("--eval-drums", type=int, default=3)
+    ap.add_argument("--noise-v", type=float, default=0.1, help="input velocity noise, in velocity scales")
+    ap.add_argument("--noise-x", type=float, default=0.0, help="input position noise, in diameters")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--max-overlap", type=float, default=0.02, help="rollout: largest overlap, in diameters")
+    ap.add_argument("--overlap-factor", type=float, default=0.0,
+                    help="rollout: or this times the largest overlap of the last DEM state")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     dev = torch.device("cuda")
     t0 = time.perf_counter()
     net = SG.SurrogateNet()
-    train = SG.drum_trajectories(a.trajectories, a.particles, 4000, 6, 60, net)
+    train = SG.drum_trajectories(a.trajectories, a.particles, 4000, 6, 60, net, noise_v=a.noise_v,
+                                 noise_x=a.noise_x)
     SG.fit_output_scale(net, train)
     held = SG.drum_trajectories(a.held_out, a.particles, 4000, 6, 60, net, seed0=workloads.seed_for(5, 900))
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    hist = SG.train(net, train, a.epochs, lr=1e-3)
+    hist = SG.train(net, train, a.epochs, lr=a.lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     mse, zero = SG.evaluate(net, held)
@@ -65,7 +76,9 @@ def main():
                 x, v, w, act = g.state()
                 fall = surr = 0
             else:
-                (xt, vt, wt), fall, surr = SG.rollout(net, wl, g, a.eval_steps)
+                st = {}
+                (xt, vt, wt), fall, surr = SG.rollout(net, wl, g, a.eval_steps, max_overlap=a.max_overlap,
+                                                      overlap_factor=a.overlap_factor, stats=st)
                 x, v, w = xt.cpu().numpy(), vt.cpu().numpy(), wt.cpu().numpy()
                 act = np.ones(wl.n, bool)
             torch.cuda.synchronize()
@@ -73,7 +86,7 @@ def main():
             res[mode] = dict(seconds=dt, us_per_equiv_step=1e6 * dt / a.eval_steps,
                              angle_deg=angle_of_repose(x, wl.radius, act, L, dmax),
                              kinetic_energy=kinetic_energy(v, w, wl.radius, wl.cfg["density"], act),
-                             fallbacks=fall, surrogate_steps=surr)
+                             fallbacks=fall, surrogate_steps=surr, **(st if mode == "surrogate" else {}))
             g.close()
         rows.append(res)
     ang_err = [abs(r["surrogate"]["angle_deg"] - r["dem"]["angle_deg"]) for r in rows]
@@ -81,6 +94,8 @@ def main():
                                                                                        1e-30) for r in rows]
     speed = [r["dem"]["seconds"] / r["surrogate"]["seconds"] for r in rows]
     out = dict(trajectories=a.trajectories, samples=len(train), particles=a.particles, epochs=a.epochs,
+               noise_v=a.noise_v, noise_x=a.noise_x, lr=a.lr, max_overlap=a.max_overlap,
+               overlap_factor=a.overlap_factor,
                seconds_data=t_data, seconds_train=t_train, loss_history=hist,
                held_out_mse=mse, held_out_mse_no_change=zero, eval_equiv_steps=a.eval_steps, drums=rows,
                angle_error_deg=ang_err, kinetic_energy_rel_error=ke_err, speed_vs_dem=speed)
