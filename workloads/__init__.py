@@ -364,6 +364,12 @@ def instance_workload(batch: Workload, k: int) -> Workload:
                     batch.w[lo:hi].copy(), batch.radius[lo:hi].copy())
 
 
+def dam_break_depth(n: int, d: float = 1e-3) -> float:
+    """Depth of the dam-break box for n spheres: 0.01 m per 160,000 spheres, the paper's
+    weak-scaling rule (Table weak_scaling), and at least four diameters."""
+    return max(0.01 * n / 160_000, 4.0 * d)
+
+
 def dam_break(n: int = 160_000, seed: int | None = None, d: float = 1e-3, length: float = 0.2,
               height: float = 0.3, t_dam: float = 0.05, precision: str = "mixed", spacing: float = 1.05,
               jitter: float = 0.02, depth: float | None = None) -> Workload:
@@ -377,7 +383,7 @@ def dam_break(n: int = 160_000, seed: int | None = None, d: float = 1e-3, length
     cube; dt = 4e-6 s (about a tenth of the Rayleigh time of a 1 mm sphere)."""
     rng = np.random.Generator(np.random.PCG64(seed_for(6) if seed is None else seed))
     if depth is None:
-        depth = max(0.01 * n / 160_000, 4.0 * d)
+        depth = dam_break_depth(n, d)
     r = 0.5 * d
     a = spacing * d
     half = 0.5 * length
