@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["silo", "drum", "dam"], default="silo")
     p.add_argument("--n", type=int, default=None, help="override the particle count (smaller runs)")
+    p.add_argument("--skin", type=float, default=None,
+                   help="override the search skin, in largest diameters (analysis runs only)")
     p.add_argument("--fp64-steps", type=int, default=None)
     p.add_argument("--profile-steps", type=int, default=None)
     p.add_argument("--no-fp64", action="store_true")
@@ -266,6 +268,9 @@ def run_reference(args):
     if rank != 0:
         return
     wl, desc = make_workload(args.workload, args.n, "mixed")
+    if args.skin is not None:
+        wl.cfg["skin"] = args.skin * 2.0 * float(wl.radius.max())
+        desc += f"-skin{args.skin:g}d"
     budget = 120.0
     rate, k, steps, dt = oracle_rate(wl, budget, max_steps=args.steps, warmup=args.warmup)
     line = {
@@ -353,6 +358,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl, desc = make_workload(args.workload, args.n, "mixed")
+    if args.skin is not None:
+        wl.cfg["skin"] = args.skin * 2.0 * float(wl.radius.max())
+        desc += f"-skin{args.skin:g}d"
     n = wl.n
     extra = {}
 
