@@ -347,13 +347,12 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k_gemm_tc(const __grid_const
   }
 }
 
+// SMs of the current device (queried on every launch: the library may serve several GPUs).
 int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-  }
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess || sms <= 0)
+    sms = 1;
   return sms;
 }
 
@@ -376,13 +375,10 @@ bool launch(const Args& a, cudaStream_t s) {
   // at least 80 KB, so that no more than two CTAs (512 columns of tensor memory) share an SM
   size_t smem = 1024 + (size_t)(nkb + ns) * kStageBytes;
   if (smem < 80 * 1024) smem = 80 * 1024;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             1024 + (kMaxKStages + kMaxStages) * kStageBytes) != cudaSuccess)
-      return false;
-    attr = true;
-  }
+  // the attribute belongs to the current device's copy of the kernel: set it on every launch
+  if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           1024 + (kMaxKStages + kMaxStages) * kStageBytes) != cudaSuccess)
+    return false;
   const int64_t tiles = (a.M + TM - 1) / TM;
   const int64_t cap = 2 * (int64_t)sm_count();
   const int grid = (int)(tiles < cap ? tiles : cap);
