@@ -387,8 +387,10 @@ def run_ours(args):
     active = 0.5 * (st0["n_active"] + st1["n_active"])
     value = job_rate(active * args.steps, ms, world)
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
-    # k_set_remaining and k_end per dem_step call, k_begin and the step kernel per step
-    launches = 2 + 2 * args.steps + REBUILD_KERNELS * rebuilds
+    inner_builds = st1["inner_builds"] - st0["inner_builds"]
+    # k_set_remaining and k_end per dem_step call, k_begin and the step kernel per step, and
+    # the list builds (a contact search also refreshes the inner list)
+    launches = 2 + 2 * args.steps + (REBUILD_KERNELS + 1) * rebuilds + max(inner_builds - rebuilds, 0)
 
     # ---------------- step-kernel roofline (CUDA events around each launch)
     kp = args.profile_steps if args.profile_steps is not None else min(args.steps, 200)
@@ -405,10 +407,13 @@ def run_ours(args):
                 "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": alg,
                 "bytes_per_particle_step": alg / max(st2["n_active"], 1),
                 "search_ms_avg": prof["search_ms"] / max(prof["searches"], 1), "searches": prof["searches"],
+                "inner_build_ms_avg": prof["inner_ms"] / max(prof["inner_builds"], 1),
+                "inner_builds": prof["inner_builds"],
                 "profiled_steps": kp, "step_share_of_time": prof["step_kernel_ms"] /
-                max(prof["step_kernel_ms"] + prof["search_ms"], 1e-12)}
+                max(prof["step_kernel_ms"] + prof["search_ms"] + prof["inner_ms"], 1e-12)}
     contacts = {"n_pairs": st2["n_pairs"], "n_touch": st2["n_touch"], "n_wall_touch": st2["n_wall_touch"],
-                "rebuilds_in_window": rebuilds, "max_overlap_ratio": st2["max_overlap_ratio"]}
+                "rebuilds_in_window": rebuilds, "inner_builds_in_window": inner_builds,
+                "max_overlap_ratio": st2["max_overlap_ratio"]}
 
     # ---------------- end to end through the C ABI with host buffers
     e2e = None

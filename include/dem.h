@@ -155,6 +155,10 @@ typedef struct {
   uint32_t status_bits;       /* sticky device flags: 1 capacity, 2 non-finite, 4 overlap, 8 timeout */
   int32_t max_neighbors_seen; /* largest fine-search list of one particle at the last rebuild */
   size_t required_workspace;  /* bytes dem_workspace_bytes reports for this configuration */
+  int64_t inner_builds;       /* mixed contexts: refreshes of the inner list, the pairs of the
+                                 fine-search list within R_i + R_j + delta (delta = min(0.1 d_max,
+                                 skin / 4)) that the force kernel walks; refreshed when a particle
+                                 has moved delta / 2, and at each contact search */
 } dem_stats;
 
 typedef struct dem_ctx dem_ctx;
@@ -192,9 +196,10 @@ dem_status dem_step(dem_ctx* ctx, int64_t n_steps);
  * every launch of the force-and-integration kernel and around every contact search; the
  * host waits for each step's search decision.  Outputs (any may be NULL): summed device
  * milliseconds of the step kernel and of the searches, the number of step-kernel
- * launches and of searches.  Synchronises. */
+ * launches and of searches, and the summed milliseconds and number of inner-list builds
+ * (mixed contexts; see dem_stats.inner_builds).  Synchronises. */
 dem_status dem_step_profiled(dem_ctx* ctx, int64_t n_steps, double* step_kernel_ms, double* search_ms,
-                             int64_t* step_launches, int64_t* searches);
+                             int64_t* step_launches, int64_t* searches, double* inner_ms, int64_t* inner_builds);
 
 /* Blocks until the context's stream is idle; reports sticky device errors. */
 dem_status dem_sync(dem_ctx* ctx);

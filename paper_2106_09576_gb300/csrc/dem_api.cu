@@ -125,7 +125,8 @@ dem_status derive(const dem_config* c, Derived* d) {
 }
 
 struct Offsets {
-  size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], inst[2], itab, xref, nbr, nbr_cnt, key, local, order,
+  size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], inst[2], itab, xref, nbr, nbr_cnt,
+      inner, inner_cnt, xin, key, local, order,
       cell_count, cell_start, scan_tmp, hkey, hval, wall_tmp, wall_tmp_mask, out_v, out_w, out_F, out_M,
       stage, ctl, io_cnt, io_off;
   size_t total;
@@ -155,6 +156,12 @@ Offsets layout(const dem_config* c, const Derived& d) {
   o.xref = L.add(3 * n * 8);
   o.nbr = L.add(n * kMaxNbr * 4);
   o.nbr_cnt = L.add(n * 4);
+  {
+    const bool mixed = c->precision == DEM_PRECISION_MIXED;   // the inner list of the mixed path
+    o.inner = L.add(mixed ? n * kInnerMax : 0);
+    o.inner_cnt = L.add(mixed ? n : 0);
+    o.xin = L.add(mixed ? 7 * n * 4 : 0);
+  }
   o.key = L.add(n * 4);
   o.local = L.add(n * 4);
   o.order = L.add(n * 4);
@@ -180,7 +187,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
 
 // ------------------------------------------------------------------ small kernels
 __global__ void k_begin(Params P, cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_reb,
-                        int in_graph) {
+                        cudaGraphConditionalHandle h_inner, int in_graph) {
   Control* C = P.ctl;
   apply_flip(C);   // the previous evaluation's parities
   const long long rem = C->remaining;
@@ -190,10 +197,13 @@ __global__ void k_begin(Params P, cudaGraphConditionalHandle h_loop, cudaGraphCo
     C->step++;
     C->since_rebuild++;
   }
-  const int need = (C->init || C->need_rebuild || (P.rebuild_every > 0 && C->since_rebuild >= P.rebuild_every))
-                       ? 1
-                       : 0;
+  const int need =
+      (C->init || C->need_rebuild || (P.rebuild_every > 0 && C->since_rebuild >= P.rebuild_every)) ? 1 : 0;
+  // the inner list (mixed path) is refreshed by every contact search, else when due
+  const int inner = (P.precision == DEM_PRECISION_MIXED && C->need_inner && !need) ? 1 : 0;
+  if (need || inner) C->need_inner = 0;
   C->do_rebuild = need;
+  C->do_inner = inner;
   // walls present at the time of this evaluation (floating walls, Sec. 3.6)
   const double t = (double)C->step * P.dt;
   unsigned on = 0u;
@@ -206,6 +216,7 @@ __global__ void k_begin(Params P, cudaGraphConditionalHandle h_loop, cudaGraphCo
   C->max_ovl_bits = 0u;
   if (in_graph) {
     cudaGraphSetConditional(h_reb, (unsigned)need);
+    cudaGraphSetConditional(h_inner, (unsigned)inner);
     cudaGraphSetConditional(h_loop, rem - 1 > 0 ? 1u : 0u);
   }
 }
@@ -538,7 +549,7 @@ void destroy_graph(dem_ctx* c) {
   c->exec = nullptr;
 }
 
-// WHILE(loop) { k_begin -> IF(rebuild) { rebuild } -> k_step } -> k_end
+// WHILE(loop) { k_begin -> IF(rebuild) { rebuild } -> IF(inner) { inner build } -> k_step } -> k_end
 dem_status build_graph(dem_ctx* c) {
   destroy_graph(c);
   cudaGraph_t g = nullptr;
@@ -546,9 +557,10 @@ dem_status build_graph(dem_ctx* c) {
   dem_status st = DEM_ERR_CUDA;
   do {
     if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
-    cudaGraphConditionalHandle hl, hr;
+    cudaGraphConditionalHandle hl, hr, hi;
     if (cudaGraphConditionalHandleCreate(&hl, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) break;
     if (cudaGraphConditionalHandleCreate(&hr, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) break;
+    if (cudaGraphConditionalHandleCreate(&hi, g, 0, cudaGraphCondAssignDefault) != cudaSuccess) break;
     cudaGraphNodeParams wp = {};
     wp.type = cudaGraphNodeTypeConditional;
     wp.conditional.handle = hl;
@@ -561,7 +573,7 @@ dem_status build_graph(dem_ctx* c) {
     if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
       break;
-    k_begin<<<1, 1, 0, cs>>>(c->P, hl, hr, 1);
+    k_begin<<<1, 1, 0, cs>>>(c->P, hl, hr, hi, 1);
     if (cudaStreamEndCapture(cs, &body) != cudaSuccess) break;
     size_t nn = 0;
     if (cudaGraphGetNodes(body, nullptr, &nn) != cudaSuccess || nn != 1) break;
@@ -580,7 +592,21 @@ dem_status build_graph(dem_ctx* c) {
       break;
     launch_rebuild(c->P, cs);
     if (cudaStreamEndCapture(cs, &rbody) != cudaSuccess) break;
-    if (cudaStreamBeginCaptureToGraph(cs, body, &inode, nullptr, 1, cudaStreamCaptureModeThreadLocal) !=
+    // IF(inner list due) { inner build } after the search's IF
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hi;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t nnode;
+    if (cudaGraphAddNode(&nnode, body, &inode, nullptr, 1, &np) != cudaSuccess) break;
+    cudaGraph_t ibody = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      break;
+    launch_inner(c->P, cs);
+    if (cudaStreamEndCapture(cs, &ibody) != cudaSuccess) break;
+    if (cudaStreamBeginCaptureToGraph(cs, body, &nnode, nullptr, 1, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
       break;
     launch_step(c->P, cs);
@@ -616,11 +642,13 @@ dem_status run_eager(dem_ctx* c, long long n_steps) {
   CK(cudaMemcpyAsync(&rem, &c->P.ctl->remaining, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   for (long long it = 0; it < rem; it++) {
-    k_begin<<<1, 1, 0, c->stream>>>(c->P, 0, 0, 0);
-    int need = 0;
+    k_begin<<<1, 1, 0, c->stream>>>(c->P, 0, 0, 0, 0);
+    int need = 0, inner = 0;
     CK(cudaMemcpyAsync(&need, &c->P.ctl->do_rebuild, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&inner, &c->P.ctl->do_inner, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (need) launch_rebuild(c->P, c->stream);
+    if (inner) launch_inner(c->P, c->stream);
     launch_step(c->P, c->stream);
   }
   k_end<<<1, 1, 0, c->stream>>>(c->P);
@@ -773,6 +801,14 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   P.f_dt = (float)P.dt;
   for (int a = 0; a < 3; a++) P.f_g[a] = (float)P.g[a];
   P.f_disp_lim2 = (float)(P.disp_lim2 * (1.0 - 1e-5));   // conservative: rebuild slightly early
+  {
+    // inner list (mixed path): the pairs of the fine-search list within R_i + R_j + delta,
+    // refreshed when a particle has moved delta / 2
+    const double delta = std::min(0.1 * d.dmax, 0.25 * d.skin);
+    P.f_inner_margin = (float)delta;
+    P.f_inner_lim2 = (float)(0.25 * delta * delta * (1.0 - 1e-5));
+    P.f_disp_lim = (float)(0.5 * d.skin);
+  }
   P.f_rc = (float)d.rc;
   P.step_block = cfg->step_block;
   P.n_inst = cfg->n_instances > 1 ? cfg->n_instances : 0;
@@ -799,6 +835,9 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   P.xref = (double*)(base + o.xref);
   P.nbr = (int*)(base + o.nbr);
   P.nbr_cnt = (int*)(base + o.nbr_cnt);
+  P.inner = (uint8_t*)(base + o.inner);
+  P.inner_cnt = (uint8_t*)(base + o.inner_cnt);
+  P.xin = (float*)(base + o.xin);
   P.key = (unsigned*)(base + o.key);
   P.local = (int*)(base + o.local);
   P.order = (int*)(base + o.order);
@@ -915,14 +954,14 @@ dem_status dem_step(dem_ctx* c, int64_t n_steps) {
 }
 
 dem_status dem_step_profiled(dem_ctx* c, int64_t n_steps, double* step_kernel_ms, double* search_ms,
-                             int64_t* step_launches, int64_t* searches) {
+                             int64_t* step_launches, int64_t* searches, double* inner_ms, int64_t* inner_builds) {
   if (c && c->P.n_inst > 1 && !c->instances_set) return DEM_ERR_STATE;
   if (!c || n_steps < 0) return DEM_ERR_ARG;
   if (c->sticky) return DEM_ERR_STATE;
-  double ks = 0.0, ss = 0.0;
-  int64_t nk = 0, ns = 0;
+  double ks = 0.0, ss = 0.0, is = 0.0;
+  int64_t nk = 0, ns = 0, ni = 0;
   if (n_steps > 0) {
-    cudaEvent_t e[4];
+    cudaEvent_t e[6];
     for (auto& ev : e)
       if (cudaEventCreate(&ev) != cudaSuccess) return DEM_ERR_CUDA;
     dem_status st = DEM_OK;
@@ -933,9 +972,11 @@ dem_status dem_step_profiled(dem_ctx* c, int64_t n_steps, double* step_kernel_ms
         cudaStreamSynchronize(c->stream) != cudaSuccess)
       st = DEM_ERR_CUDA;
     for (long long it = 0; st == DEM_OK && it < rem; it++) {
-      k_begin<<<1, 1, 0, c->stream>>>(c->P, 0, 0, 0);
-      int need = 0;
+      k_begin<<<1, 1, 0, c->stream>>>(c->P, 0, 0, 0, 0);
+      int need = 0, inner = 0;
       if (cudaMemcpyAsync(&need, &c->P.ctl->do_rebuild, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(&inner, &c->P.ctl->do_inner, sizeof(int), cudaMemcpyDeviceToHost, c->stream) !=
               cudaSuccess ||
           cudaStreamSynchronize(c->stream) != cudaSuccess) {
         st = DEM_ERR_CUDA;
@@ -945,6 +986,11 @@ dem_status dem_step_profiled(dem_ctx* c, int64_t n_steps, double* step_kernel_ms
         cudaEventRecord(e[2], c->stream);
         launch_rebuild(c->P, c->stream);
         cudaEventRecord(e[3], c->stream);
+      }
+      if (inner) {
+        cudaEventRecord(e[4], c->stream);
+        launch_inner(c->P, c->stream);
+        cudaEventRecord(e[5], c->stream);
       }
       cudaEventRecord(e[0], c->stream);
       launch_step(c->P, c->stream);
@@ -962,6 +1008,11 @@ dem_status dem_step_profiled(dem_ctx* c, int64_t n_steps, double* step_kernel_ms
         ss += ms;
         ns++;
       }
+      if (inner) {
+        cudaEventElapsedTime(&ms, e[4], e[5]);
+        is += ms;
+        ni++;
+      }
     }
     for (auto& ev : e) cudaEventDestroy(ev);
     if (st != DEM_OK) return st;
@@ -972,6 +1023,8 @@ dem_status dem_step_profiled(dem_ctx* c, int64_t n_steps, double* step_kernel_ms
   if (search_ms) *search_ms = ss;
   if (step_launches) *step_launches = nk;
   if (searches) *searches = ns;
+  if (inner_ms) *inner_ms = is;
+  if (inner_builds) *inner_builds = ni;
   return check_sticky(c);
 }
 
@@ -1145,6 +1198,7 @@ dem_status dem_get_stats(dem_ctx* c, dem_stats* out) {
   c->sticky |= h.status;
   out->status_bits = c->sticky;
   out->max_neighbors_seen = h.max_nbr_seen;
+  out->inner_builds = h.inner_builds;
   dem_workspace_bytes(&c->cfg, &out->required_workspace);
   return DEM_OK;
 }

@@ -21,6 +21,12 @@
 //                                     bit order (parity ctl->hc)
 //     nbr               int32 [n][56] fine-search list (full list: each pair twice)
 //     nbr_cnt           int32 [n]
+//     inner, inner_cnt  uint8 [n][32], uint8 [n] (mixed path): the slots of the fine-search
+//                                     list whose partner was within R_i + R_j + delta at the
+//                                     last inner build, ascending (so in partner-id order)
+//     xin               FP32 [7][n]   (mixed path) positions at the last inner build, hi
+//                                     parts then lo parts, then the distance of that position
+//                                     from the search reference x_ref (rounded up)
 //   per cell: cell_count, cell_start (int32 [n_cells + 2])
 //   hash table of tangential overlaps used at rebuild: hkey uint64 [cap], hval FP64 [cap][3]
 #pragma once
@@ -34,6 +40,7 @@ namespace demgb {
 constexpr int kMaxWalls = 8;
 constexpr int kMaxNbr = 56;      // slots per particle in the fine-search list
 constexpr int kHistStride = 32;  // simultaneous contacts per particle (particles + walls)
+constexpr int kInnerMax = 32;    // entries of a particle's inner list (mixed path)
 constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
 
 // status bits (sticky, in Control::status)
@@ -102,6 +109,11 @@ struct Control {
   long long since_rebuild;
   long long rebuilds;
   long long remaining;  // evaluations left in the current dem_step call
+  // inner list (mixed path): a particle moved more than delta / 2 from its position at the
+  // last inner build, the decision of the current iteration, and the number of builds
+  int need_inner;
+  int do_inner;
+  long long inner_builds;
   unsigned long long n_touch_dir;   // directed particle-particle contacts, last step
   unsigned long long n_wall_touch;
   unsigned long long n_pairs_dir;   // directed fine-search entries at the last rebuild
@@ -151,6 +163,9 @@ struct Params {
   WallDev walls[kMaxWalls];
   // FP32 copies of uniform constants (mixed path), computed once on the host
   float f_density, f_dt, f_g[3], f_disp_lim2, f_rc;
+  // inner list: margin delta and (delta / 2)^2 (slightly reduced); skin / 2, below which
+  // a particle cannot fire the search trigger
+  float f_inner_margin, f_inner_lim2, f_disp_lim;
   MatF mf;
   long long z_sink_key;   // ordered-integer image of z_sink (exact comparison without FP64)
   WallF wf[kMaxWalls];
@@ -173,6 +188,9 @@ struct Params {
   float4* render[2];    // [n][3] FP32 {x_lo, flag} {v, w_x} {w_y, w_z, 0, 0}
   int* nbr;
   int* nbr_cnt;
+  uint8_t* inner;       // [n][kInnerMax] (mixed path)
+  uint8_t* inner_cnt;   // [n]
+  float* xin;           // [7][n]
   unsigned* key;        // [n] cell key of the current (pre-sort) order
   int* local;           // [n] slot within the cell
   int* order;           // [n] sorted position -> previous position
@@ -337,6 +355,7 @@ __device__ __forceinline__ int cell_coord(double xd, double lo, double inv_h, in
 
 // Launchers (host side), defined in the .cu files.
 void launch_rebuild(const Params& P, cudaStream_t s);
+void launch_inner(const Params& P, cudaStream_t s);
 void launch_hist_clear(const Params& P, cudaStream_t s, int force);
 void scan_exclusive_i32(const int* in, int n, int* out, int* partials, cudaStream_t s);
 void launch_step_fp64(const Params& P, cudaStream_t s);

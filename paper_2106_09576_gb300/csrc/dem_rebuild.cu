@@ -413,6 +413,67 @@ __global__ void k_hist_load(Params P) {
   P.mask[hn][q] = m;
 }
 
+// ------------------------------------------------------------------ 6. inner list (mixed)
+// The slots k of each particle's fine-search list whose partner lies within
+// R_i + R_j + delta, decided on the FP32 hi parts with the test widened by their error
+// bound (so no such pair is dropped), in ascending k, i.e. in partner-id order.  The
+// particle's position becomes the reference of the next refresh, stored with its distance
+// from the search reference (rounded up): the step kernel bounds a particle's move since
+// the search by that distance plus its move since the refresh, and tests the search
+// trigger exactly only when the bound comes near skin / 2.
+__global__ void k_inner_build(Params P) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  Control* C = P.ctl;
+  if (blockIdx.x == 0 && threadIdx.x == 0) C->inner_builds++;
+  const int n = P.n;
+  if (q >= n) return;
+  if (q >= C->n_act_sorted) {
+    P.inner_cnt[q] = 0;
+    return;
+  }
+  const int cur = C->cur;
+  const float4* SH = P.shadow[cur];
+  const float4 hi = SH[q];
+  const float4 lo4 = P.render[cur][3 * (size_t)q];
+  const float ai = max_abs3(hi);
+  const int* nb = P.nbr + (size_t)q * kMaxNbr;
+  const int cnt = P.nbr_cnt[q];
+  uint8_t* row = P.inner + (size_t)q * kInnerMax;
+  int m = 0;
+  bool overflow = false;
+  for (int k = 0; k < cnt; k++) {
+    const float4 hj = SH[nb[k]];
+    const float ex = hj.x - hi.x, ey = hj.y - hi.y, ez = hj.z - hi.z;
+    const float reach = hi.w + hj.w + P.f_inner_margin;
+    const float up = reach + hi_distance_error(ai, max_abs3(hj), 2.0f * reach);
+    if (ex * ex + ey * ey + ez * ez > up * up * (1.0f + 1e-6f)) continue;
+    if (m < kInnerMax)
+      row[m++] = (uint8_t)k;
+    else
+      overflow = true;
+  }
+  P.inner_cnt[q] = (uint8_t)m;
+  if (overflow) atomicOr(&C->status, kStCapacity);
+  const float* xr = reinterpret_cast<const float*>(P.xref);
+  const float h[3] = {hi.x, hi.y, hi.z}, l[3] = {lo4.x, lo4.y, lo4.z};
+  float d2 = 0.0f;
+  for (int d = 0; d < 3; d++) {
+    float s1, t1;
+    df_diff(xr[d * n + q], xr[(3 + d) * n + q], h[d], l[d], s1, t1);
+    const float u = s1 + t1;
+    d2 += u * u;
+    P.xin[d * n + q] = h[d];
+    P.xin[(3 + d) * n + q] = l[d];
+  }
+  P.xin[6 * n + q] = sqrtf(d2) * (1.0f + 1e-5f);
+}
+
+void launch_inner(const Params& P, cudaStream_t s) {
+  if (P.precision != DEM_PRECISION_MIXED) return;
+  const int T = 256;
+  k_inner_build<<<(P.n + T - 1) / T, T, 0, s>>>(P);
+}
+
 __global__ void k_rebuild_begin(Params P) {
   Control* C = P.ctl;
   C->max_nbr_seen = 0;
@@ -469,6 +530,8 @@ void launch_rebuild(const Params& P, cudaStream_t s) {
   // 5. history
   k_hist_load<<<nb, T, 0, s>>>(P);
   k_rebuild_end<<<1, 1, 0, s>>>(P);
+  // 6. the inner list of the mixed path, drawn from the new list
+  launch_inner(P, s);
 }
 
 }  // namespace demgb

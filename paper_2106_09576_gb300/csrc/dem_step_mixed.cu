@@ -1,11 +1,13 @@
 // dem_step_mixed.cu -- mixed-precision step kernel: FP32 contact law, FP64 positions,
 // velocities, integration and tangential-overlap accumulation.
 //
-// One thread owns one particle of the cell-sorted order and walks its fine-search list.
+// One thread owns one particle of the cell-sorted order and walks its inner list (the pairs
+// of its fine-search list within R_i + R_j + delta, refreshed before any particle moves
+// delta / 2).
 // FP64 instructions issue at 1/72 of the FP32 rate on this part, so the kernel keeps them
 // to the integration (9 FMAs per particle) and the tangential-overlap accumulation
 // (3 adds per contact).  Every particle publishes, once per step, FP32 copies of itself
-// for its neighbours: a 16-byte shadow {x_hi, R} that the contact prefilter reads, and a
+// for its neighbours: a 16-byte shadow {x_hi, R} that the list builds read, and a
 // 48-byte render {x_lo, in-system flag, v, w} that a contact partner reads; its own
 // thread starts from them too and reads its FP64 state only for walls and integration.
 //   - relative positions are exact two-sum differences of the hi + lo pairs, so nearly
@@ -143,37 +145,17 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
     } else {
       const int* nb = P.nbr + (size_t)i * kMaxNbr;
-      const int cnt = P.nbr_cnt[i];
       const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o1.x, o1.y, o1.z};
       const float Rif = o0.w;
       // materials and walls: the context's, or those of the particle's instance in a batch
       const InstDev* I = kBatch ? P.itab + P.inst[C->sbuf][i] : nullptr;
       const MatF& Mt = kBatch ? I->mf : P.mf;
       // ---------------- particle-particle contacts
-      // (a) Prefilter on the FP32 hi parts, 8 list entries at a time: two 16-byte loads of
-      //     indices, then 8 independent 16-byte shadow loads.  hi truncates x to 24
-      //     significant bits: |x - hi| < 2^-23 |x|, so a coordinate difference of two hi
-      //     parts (partners within r_c) is off by less than 2^-23 (2 |x_i| + 2 r_c),
-      //     rounding included; the test is widened by sqrt(3) times that bound, so it
-      //     cannot drop a contact.
-      const float amax = fmaxf(fmaxf(fabsf(hx[0]), fabsf(hx[1])), fabsf(hx[2]));
-      const float slack = 1.7320508f * 1.1920929e-7f * (2.0f * amax + 2.0f * P.f_rc) + 1e-30f;
-      const int4* nb4 = reinterpret_cast<const int4*>(nb);
-      unsigned long long cand = 0ull;
-      for (int k0 = 0; k0 < cnt; k0 += 8) {
-        const int4 ja = nb4[k0 >> 2], jb = nb4[(k0 >> 2) + 1];   // row has 56 slots: in bounds
-        const int js[8] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y, jb.z, jb.w};
-        float4 sh[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++)
-          sh[u] = (k0 + u < cnt) ? SH[js[u]] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-          const float ex = sh[u].x - hx[0], ey = sh[u].y - hx[1], ez = sh[u].z - hx[2];
-          const float reach = (Rif + sh[u].w + slack) * 1.000001f;
-          if (k0 + u < cnt && ex * ex + ey * ey + ez * ez < reach * reach) cand |= 1ull << (k0 + u);
-        }
-      }
+      // The inner list holds the slots of the fine-search list whose partner was within
+      // R_i + R_j + delta when it was built; no particle has moved delta / 2 since, so it
+      // holds every touching pair, in partner-id order (a serial pair loop's order).
+      const uint8_t* irow = P.inner + (size_t)i * kInnerMax;
+      const int icnt = P.inner_cnt[i];
       const float4 o2 = RD[3 * (size_t)i + 1], o3 = RD[3 * (size_t)i + 2];
       const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
       const unsigned long long mold = P.mask[hc][i];
@@ -185,10 +167,9 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       unsigned long long mnew = 0ull;
       int rank = 0;
 
-      // (b) candidates in list order; every load of a candidate is issued before any branch
-      while (cand) {
-        const int k = __ffsll((long long)cand) - 1;
-        cand &= cand - 1ull;
+      // every load of a candidate is issued before any branch
+      for (int slot = 0; slot < icnt; slot++) {
+        const int k = irow[slot];
         const int j = nb[k];
         const float4 r0 = SH[j];
         const float4* rj = RD + 3 * (size_t)j;
@@ -232,7 +213,11 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         const float wj[3] = {r2.w, r3.x, r3.y};
         const float dv[3] = {vif[0] - r2.x, vif[1] - r2.y, vif[2] - r2.z};
         const float dw[3] = {wif[0] - wj[0], wif[1] - wj[1], wif[2] - wj[2]};
-        const float rw[3] = {Rif * wif[0] + Rjf * wj[0], Rif * wif[1] + Rjf * wj[1], Rif * wif[2] + Rjf * wj[2]};
+        // R_i w_i + R_j w_j rounded identically on both sides of the pair (no contraction),
+        // so the two sides' tangential overlaps stay exact opposites and a contact search,
+        // which restores one side's overlap from the other's, leaves the trajectory unchanged
+        float rw[3];
+        for (int d = 0; d < 3; d++) rw[d] = __fadd_rn(__fmul_rn(Rif, wif[d]), __fmul_rn(Rjf, wj[d]));
         // (R_i w_i + R_j w_j) x n: part of v_ij, and V_omega of the viscous rolling model
         const float rwxn[3] = {rw[1] * nrm[2] - rw[2] * nrm[1], rw[2] * nrm[0] - rw[0] * nrm[2],
                                rw[0] * nrm[1] - rw[1] * nrm[0]};
@@ -339,9 +324,11 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         st.status |= kStNonfinite;
       if (alive) {
         st.active++;
-        // dynamic search trigger |x^{n+1} - x_ref|^2 > (skin/2)^2 without FP64 arithmetic;
-        // x_ref is kept as its hi + lo pair
-        const float* xr = reinterpret_cast<const float*>(P.xref);
+        // triggers on the hi + lo pairs, without FP64 arithmetic: the inner list is due when
+        // |x^{n+1} - x_in| > delta / 2; the contact search (as the method states it) when
+        // |x^{n+1} - x_ref| > skin / 2, which is tested only when |x^{n+1} - x_in| plus the
+        // stored |x_in - x_ref| come near skin / 2 (below, it cannot hold)
+        const float* xr = P.xin;
         float d2 = 0.f;
         for (int d = 0; d < 3; d++) {
           float s1, t1;
@@ -349,7 +336,18 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
           const float u = s1 + t1;
           d2 += u * u;
         }
-        if (P.rebuild_every <= 0 && d2 > P.f_disp_lim2) P.ctl->need_rebuild = 1;
+        if (d2 > P.f_inner_lim2) P.ctl->need_inner = 1;
+        if (P.rebuild_every <= 0 && sqrtf(d2) * (1.0f + 1e-5f) + xr[6 * n + i] > P.f_disp_lim * (1.0f - 1e-5f)) {
+          const float* xs = reinterpret_cast<const float*>(P.xref);
+          float e2 = 0.f;
+          for (int d = 0; d < 3; d++) {
+            float s1, t1;
+            df_diff(xs[d * n + i], xs[(3 + d) * n + i], hn[d], ln[d], s1, t1);
+            const float u = s1 + t1;
+            e2 += u * u;
+          }
+          if (e2 > P.f_disp_lim2) P.ctl->need_rebuild = 1;
+        }
       }
     }
   }

@@ -62,7 +62,8 @@ class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("rebuilds", C.c_int64), ("n_pairs", C.c_int64),
                 ("n_touch", C.c_int64), ("n_wall_touch", C.c_int64), ("n_active", C.c_int64),
                 ("time", C.c_double), ("max_overlap_ratio", C.c_double), ("status_bits", C.c_uint32),
-                ("max_neighbors_seen", C.c_int32), ("required_workspace", C.c_size_t)]
+                ("max_neighbors_seen", C.c_int32), ("required_workspace", C.c_size_t),
+                ("inner_builds", C.c_int64)]
 
 
 _lib = None
@@ -91,7 +92,8 @@ def load_library(build_if_missing: bool = True):
         "dem_step": [P, C.c_int64],
         "dem_sync": [P],
         "dem_step_profiled": [P, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double),
-                              C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+                              C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                              C.POINTER(C.c_int64)],
         "dem_get_state": [P, P, P, P, P],
         "dem_set_state": [P, P, P, P, P],
         "dem_get_forces": [P, P, P],
@@ -304,11 +306,12 @@ class DEM:
     def step_profiled(self, n_steps: int):
         """Same steps as step(), launched one by one with CUDA events around the step
         kernel and the contact searches; returns the device milliseconds and counts."""
-        ks, ss = C.c_double(0), C.c_double(0)
-        nk, ns = C.c_int64(0), C.c_int64(0)
+        ks, ss, is_ = C.c_double(0), C.c_double(0), C.c_double(0)
+        nk, ns, ni = C.c_int64(0), C.c_int64(0), C.c_int64(0)
         _check(self.lib, "dem_step_profiled", self.lib.dem_step_profiled(
-            self.h, int(n_steps), C.byref(ks), C.byref(ss), C.byref(nk), C.byref(ns)))
-        return dict(step_kernel_ms=ks.value, search_ms=ss.value, step_launches=nk.value, searches=ns.value)
+            self.h, int(n_steps), C.byref(ks), C.byref(ss), C.byref(nk), C.byref(ns), C.byref(is_), C.byref(ni)))
+        return dict(step_kernel_ms=ks.value, search_ms=ss.value, step_launches=nk.value, searches=ns.value,
+                    inner_ms=is_.value, inner_builds=ni.value)
 
     def sync(self):
         _check(self.lib, "dem_sync", self.lib.dem_sync(self.h))

@@ -79,20 +79,27 @@ def test_silo_discharge_rate_and_packing_mixed_vs_fp64():
 
 
 def test_drum_dynamic_angle_of_repose_mixed_vs_fp64():
+    # Each precision's angle is one draw of a chaotic flow: two realizations per seed (the
+    # second with the initial positions moved by up to 1 nm) so that the comparison has
+    # six samples a side; one sample per seed gave offsets of 1-1.5 degrees by chance.
     angles = {"fp64": [], "mixed": []}
     for seed in (4301, 4302, 4303):
         for prec in ("fp64", "mixed"):
-            wl = workloads.drum(n=2500, seed=seed, omega=3.0, precision=prec)
-            wl.cfg["dt"] = 1e-5
-            g = make_gpu(wl, prec)
-            g.step(30000)
-            samples = []
-            for _ in range(10):
-                g.step(3000)
-                x, _, _, act = g.state()
-                samples.append(angle_of_repose(x, wl.radius, act, wl.cfg["drum_length"], 2 * float(wl.radius.max())))
-            angles[prec].append(float(np.mean(samples)))
-            g.close()
+            for rep in range(2):
+                wl = workloads.drum(n=2500, seed=seed, omega=3.0, precision=prec)
+                wl.cfg["dt"] = 1e-5
+                if rep:
+                    wl.x = wl.x + np.random.default_rng(rep).uniform(-1e-9, 1e-9, wl.x.shape)
+                g = make_gpu(wl, prec)
+                g.step(30000)
+                samples = []
+                for _ in range(10):
+                    g.step(3000)
+                    x, _, _, act = g.state()
+                    samples.append(angle_of_repose(x, wl.radius, act, wl.cfg["drum_length"],
+                                                   2 * float(wl.radius.max())))
+                angles[prec].append(float(np.mean(samples)))
+                g.close()
     af, am = np.array(angles["fp64"]), np.array(angles["mixed"])
     se = np.sqrt(af.var(ddof=1) / len(af) + am.var(ddof=1) / len(am))
     print(f"dynamic angle of repose fp64 {af} mixed {am} (deg); standard error {se:.3f}")
