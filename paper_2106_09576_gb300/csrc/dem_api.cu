@@ -126,7 +126,7 @@ dem_status derive(const dem_config* c, Derived* d) {
 
 struct Offsets {
   size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], inst[2], itab, xref, nbr, nbr_cnt,
-      inner, inner_cnt, xin, key, local, order,
+      inner, inner_j, inner_cnt, xin, key, local, order,
       cell_count, cell_start, scan_tmp, hkey, hval, wall_tmp, wall_tmp_mask, out_v, out_w, out_F, out_M,
       stage, ctl, io_cnt, io_off;
   size_t total;
@@ -159,6 +159,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
   {
     const bool mixed = c->precision == DEM_PRECISION_MIXED;   // the inner list of the mixed path
     o.inner = L.add(mixed ? n * kInnerMax : 0);
+    o.inner_j = L.add(mixed ? n * kInnerMax * 4 : 0);
     o.inner_cnt = L.add(mixed ? n : 0);
     o.xin = L.add(mixed ? 7 * n * 4 : 0);
   }
@@ -836,6 +837,7 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   P.nbr = (int*)(base + o.nbr);
   P.nbr_cnt = (int*)(base + o.nbr_cnt);
   P.inner = (uint8_t*)(base + o.inner);
+  P.inner_j = (int*)(base + o.inner_j);
   P.inner_cnt = (uint8_t*)(base + o.inner_cnt);
   P.xin = (float*)(base + o.xin);
   P.key = (unsigned*)(base + o.key);

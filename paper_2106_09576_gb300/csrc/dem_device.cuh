@@ -24,6 +24,7 @@
 //     inner, inner_cnt  uint8 [n][32], uint8 [n] (mixed path): the slots of the fine-search
 //                                     list whose partner was within R_i + R_j + delta at the
 //                                     last inner build, ascending (so in partner-id order)
+//     inner_j           int32 [n][32] (mixed path) the partners of those slots
 //     xin               FP32 [7][n]   (mixed path) positions at the last inner build, hi
 //                                     parts then lo parts, then the distance of that position
 //                                     from the search reference x_ref (rounded up)
@@ -189,6 +190,7 @@ struct Params {
   int* nbr;
   int* nbr_cnt;
   uint8_t* inner;       // [n][kInnerMax] (mixed path)
+  int* inner_j;         // [n][kInnerMax] partner of each inner slot
   uint8_t* inner_cnt;   // [n]
   float* xin;           // [7][n]
   unsigned* key;        // [n] cell key of the current (pre-sort) order

@@ -439,18 +439,23 @@ __global__ void k_inner_build(Params P) {
   const int* nb = P.nbr + (size_t)q * kMaxNbr;
   const int cnt = P.nbr_cnt[q];
   uint8_t* row = P.inner + (size_t)q * kInnerMax;
+  int* rowj = P.inner_j + (size_t)q * kInnerMax;
   int m = 0;
   bool overflow = false;
   for (int k = 0; k < cnt; k++) {
-    const float4 hj = SH[nb[k]];
+    const int j = nb[k];
+    const float4 hj = SH[j];
     const float ex = hj.x - hi.x, ey = hj.y - hi.y, ez = hj.z - hi.z;
     const float reach = hi.w + hj.w + P.f_inner_margin;
     const float up = reach + hi_distance_error(ai, max_abs3(hj), 2.0f * reach);
     if (ex * ex + ey * ey + ez * ez > up * up * (1.0f + 1e-6f)) continue;
-    if (m < kInnerMax)
-      row[m++] = (uint8_t)k;
-    else
+    if (m < kInnerMax) {
+      row[m] = (uint8_t)k;
+      rowj[m] = j;
+      m++;
+    } else {
       overflow = true;
+    }
   }
   P.inner_cnt[q] = (uint8_t)m;
   if (overflow) atomicOr(&C->status, kStCapacity);

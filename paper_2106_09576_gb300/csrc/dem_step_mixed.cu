@@ -144,7 +144,6 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       SHo[i] = o0;
       for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
     } else {
-      const int* nb = P.nbr + (size_t)i * kMaxNbr;
       const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o1.x, o1.y, o1.z};
       const float Rif = o0.w;
       // materials and walls: the context's, or those of the particle's instance in a batch
@@ -155,6 +154,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       // R_i + R_j + delta when it was built; no particle has moved delta / 2 since, so it
       // holds every touching pair, in partner-id order (a serial pair loop's order).
       const uint8_t* irow = P.inner + (size_t)i * kInnerMax;
+      const int* jrow = P.inner_j + (size_t)i * kInnerMax;
       const int icnt = P.inner_cnt[i];
       const float4 o2 = RD[3 * (size_t)i + 1], o3 = RD[3 * (size_t)i + 2];
       const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       // every load of a candidate is issued before any branch
       for (int slot = 0; slot < icnt; slot++) {
         const int k = irow[slot];
-        const int j = nb[k];
+        const int j = jrow[slot];
         const float4 r0 = SH[j];
         const float4* rj = RD + 3 * (size_t)j;
         const float4 r1 = rj[0], r2 = rj[1], r3 = rj[2];
