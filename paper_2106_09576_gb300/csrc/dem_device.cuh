@@ -10,8 +10,8 @@
 //     shadow[2]         float4 [n]    {hx, hy, hz, R} of each particle: written at each
 //                                     contact search (the FP32 filters of the fine search
 //                                     and the history restore read it) and, in a mixed
-//                                     context, by every step (the contact prefilter reads
-//                                     it); ping-pong with the state
+//                                     context, by every step (the inner-list builds and
+//                                     the contact partners read it); ping-pong with the state
 //     render[2]         float4 [n][3] {lx, ly, lz, in-system} {vx, vy, vz, wx}
 //                                     {wy, wz, 0, 0} (mixed path): what a contact partner
 //                                     reads; x = hx + lx to 2^-48; ping-pong with the state
