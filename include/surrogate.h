@@ -110,6 +110,14 @@ int surr_gemm_bf16_tc(const void* A, const void* B, float* C, int64_t M, int64_t
  * loaded (synchronises the device; 0 in normal operation). */
 int surr_tc_timeouts(int* count);
 
+/* Self-test of the bound on the tensor-core kernel's waits: one CTA of 128 threads waits on
+ * a barrier that nothing arrives on.  Every wait gives up (gave_up = 128) after the bound or
+ * through the CTA's abort flag, the threads that reached the bound first are counted
+ * (timed_out >= 1), and the kernel returns; the counter of surr_tc_timeouts is not touched.
+ * Results pass through a file-scope device array (one probe at a time per device);
+ * synchronises the device. */
+int surr_tc_wait_probe(int* gave_up, int* timed_out);
+
 #ifdef __cplusplus
 }
 #endif

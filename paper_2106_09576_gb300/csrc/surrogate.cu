@@ -723,6 +723,11 @@ extern "C" int surr_gemm_bf16_tc(const void* A, const void* B, float* C, int64_t
   return surrtc::launch(a, (cudaStream_t)stream) ? 0 : 2;
 }
 
+extern "C" int surr_tc_wait_probe(int* gave_up, int* timed_out) {
+  if (!gave_up || !timed_out) return 1;
+  return surrtc::wait_probe(gave_up, timed_out) ? 0 : 2;
+}
+
 extern "C" int surr_tc_timeouts(int* count) {
   if (!count) return 1;
   *count = surrtc::timeouts();

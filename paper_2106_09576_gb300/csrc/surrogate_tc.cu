@@ -34,6 +34,7 @@ constexpr int kMaxStages = 4;              // A stages in flight at most
 constexpr long long kSpinLimit = 1ll << 18;  // try_wait calls per wait (each may sleep)
 
 __device__ int g_timeouts;
+__device__ int g_probe[2];   // wait_probe's results (one probe at a time per device)
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B
 // (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
@@ -75,15 +76,33 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Waits for the phase of the given parity; gives up after kSpinLimit attempts, or at once
-// when another thread of the CTA has given up (so a broken pipeline unwinds quickly).
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
+// when another thread of the CTA has given up (so a broken pipeline unwinds quickly), and
+// counts the timeout in *counter.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* counter = &g_timeouts) {
   for (long long it = 0; it < kSpinLimit; it++) {
     if (mbar_try(b, parity)) return true;
     if (*abort) return false;
   }
   *abort = 1;
-  atomicAdd(&g_timeouts, 1);
+  atomicAdd(counter, 1);
   return false;
+}
+
+// Self-test of the bound: 128 threads wait on an mbarrier that nothing arrives on; every
+// wait must give up (by the bound, or through the abort flag once a thread has) and the
+// kernel must return.  out[0]: waits that gave up, out[1]: timeouts counted (the threads
+// that reached the bound before seeing the flag, at least one).
+__global__ void k_wait_probe(int* out) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0u, &abort_flag, out + 1);
+  if (!ok) atomicAdd(out, 1);
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
@@ -384,6 +403,21 @@ bool launch(const Args& a, cudaStream_t s) {
   const int grid = (int)(tiles < cap ? tiles : cap);
   k_gemm_tc<<<grid, kThreads + 32, smem, s>>>(a, ns);
   return cudaGetLastError() == cudaSuccess;
+}
+
+bool wait_probe(int* gave_up, int* timed_out) {
+  int* d = nullptr;
+  int h[2] = {0, 0};
+  bool ok = cudaGetSymbolAddress((void**)&d, g_probe) == cudaSuccess &&
+            cudaMemset(d, 0, 2 * sizeof(int)) == cudaSuccess;
+  if (ok) {
+    k_wait_probe<<<1, kThreads>>>(d);
+    ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+         cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess;
+  }
+  *gave_up = h[0];
+  *timed_out = h[1];
+  return ok;
 }
 
 int timeouts() {

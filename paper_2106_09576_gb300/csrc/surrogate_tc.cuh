@@ -38,4 +38,7 @@ bool launch(const Args& a, cudaStream_t s);
 // not written).
 int timeouts();
 
+// Self-test of the wait bound (see surr_tc_wait_probe).  False on a CUDA error.
+bool wait_probe(int* gave_up, int* timed_out);
+
 }  // namespace surrtc

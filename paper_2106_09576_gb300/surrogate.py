@@ -19,7 +19,7 @@ from . import dem as _dem
 
 K_STEPS = 10
 SURR_FUNCS = ["surr_params", "surr_workspace_bytes", "surr_build_csr", "surr_params_to_bf16", "surr_forward",
-              "surr_backward", "surr_mse", "surr_adam", "surr_gemm_bf16", "surr_gemm_bf16_tc", "surr_tc_timeouts",
+              "surr_backward", "surr_mse", "surr_adam", "surr_gemm_bf16", "surr_gemm_bf16_tc", "surr_tc_timeouts", "surr_tc_wait_probe",
               "surr_features", "surr_targets", "surr_apply"]
 
 
@@ -48,6 +48,7 @@ def lib():
         "surr_gemm_bf16": [P, P, P, I64, I64, I64, P],
         "surr_gemm_bf16_tc": [P, P, P, I64, I64, P],
         "surr_tc_timeouts": [C.POINTER(C.c_int)],
+        "surr_tc_wait_probe": [C.POINTER(C.c_int), C.POINTER(C.c_int)],
         "surr_features": [P, P, P, P, I64, P, P, I64, P, P, P, P, P],
         "surr_targets": [P, P, P, P, P, I64, P, P, P, P],
         "surr_apply": [P, P, P, P, I64, P, P, P, D, P],

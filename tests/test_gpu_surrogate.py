@@ -64,6 +64,21 @@ def test_tcgen05_rejects_shapes_outside_its_limits():
     assert SG.lib().surr_gemm_bf16_tc(None, SG._p(B), SG._p(C), 64, 16, None) == 1
 
 
+def test_tcgen05_waits_give_up_and_report():
+    """The bound on the tensor-core kernel's mbarrier waits: a barrier that nothing arrives
+    on must make every waiting thread give up, count one timeout and let the kernel return
+    (no fault, no hang); the product kernel's own timeout counter is untouched."""
+    import ctypes
+    from paper_2106_09576_gb300 import surrogate as SG
+    before = ctypes.c_int(-1)
+    assert SG.lib().surr_tc_timeouts(ctypes.byref(before)) == 0
+    gave_up, timed_out = ctypes.c_int(-1), ctypes.c_int(-1)
+    assert SG.lib().surr_tc_wait_probe(ctypes.byref(gave_up), ctypes.byref(timed_out)) == 0
+    assert gave_up.value == 128 and 1 <= timed_out.value <= 128
+    after = ctypes.c_int(-1)
+    assert SG.lib().surr_tc_timeouts(ctypes.byref(after)) == 0 and after.value == before.value
+
+
 def random_case(n=300, seed=1):
     rng = np.random.default_rng(seed)
     pts = rng.uniform(0, 1, (n, 3))
