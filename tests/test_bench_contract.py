@@ -1,0 +1,83 @@
+"""The benchmark's host side, without a GPU: the reference arm (the CPU oracle timed on a
+bounded sample) prints one well-formed JSON line on rank 0 and nothing on the other ranks,
+and the roofline's inputs (measured peak, recorded DRAM traffic, algorithmic bytes) are
+read and computed as stated."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+ARGS = ["--impl", "reference", "--n", "3000", "--steps", "2", "--warmup", "1"]
+
+
+def run_bench(extra_env=None):
+    env = dict(os.environ)
+    env.update(extra_env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + ARGS, cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=600)
+
+
+def test_reference_arm_prints_one_contract_line():
+    p = run_bench()
+    assert p.returncode == 0, p.stderr
+    lines = [s for s in p.stdout.splitlines() if s.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["dtype"] == "f64" and d["data"] == "synthetic" and d["gpu_launches"] == 0
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    # 3000 spheres fit the CPU budget, so the sample is the whole system
+    assert d["config"]["sample"] == 3000 and d["config"]["workload"].endswith("-3000")
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["unit"] == d["unit"]
+    assert "all of it" in cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    # the value is the sample's particle-steps over the timed steps
+    assert d["value"] == pytest.approx(3000 * 2 / (d["ms_per_step"] * 2 / 1e3), rel=1e-9)
+
+
+def test_reference_arm_is_silent_on_other_ranks():
+    p = run_bench({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert p.returncode == 0, p.stderr
+    assert p.stdout.strip() == ""
+
+
+def test_measured_peak_is_the_copy_bandwidth():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, kind = bench.measured_hbm_peak()
+    if os.path.exists(path):
+        with open(path) as f:
+            assert peak == float(json.load(f)["hbm_gbs"]) and kind == "measured"
+    else:
+        assert peak == bench.FALLBACK_HBM_GBS and kind == "fallback"
+
+
+def test_recorded_traffic_scales_per_particle_and_needs_the_workload():
+    t = bench.recorded_traffic("silo-packed", 4_300_000)
+    if t is None:
+        pytest.skip("no traffic line for the current step-kernel sources")
+    assert t == pytest.approx(bench.recorded_traffic("silo-packed", 2_150_000) * 2.0)
+    assert bench.recorded_traffic("drum", 4_300_000) is None
+
+
+def test_algorithmic_bytes_per_unit():
+    st = {"n_pairs": 10, "n_touch": 3, "n_wall_touch": 2}
+    assert bench.algorithmic_bytes(st, 100) == 172 * 100 + 4 * 10 + 48 * 3 + 48 * 2
+    assert bench.algorithmic_bytes({"n_pairs": 0, "n_touch": 0, "n_wall_touch": 0}, 0) == 0
+
+
+def test_job_rate_on_one_rank():
+    # 1,000 units in 250 ms: 4,000 units per second
+    assert bench.job_rate(1000.0, 250.0, 1) == pytest.approx(4000.0)
