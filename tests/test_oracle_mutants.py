@@ -70,6 +70,21 @@ MUTANTS = [
      ["test_cylinder_static_overlap_and_drum_drag"]),
     ("annulus rim ignored", "if (rho < W->inner_radius || rho > W->radius) {", "if (rho > W->radius) {",
      ["test_annulus_face_and_rim_contact_geometry"]),
+    ("tangential torque on j reversed", "s->M[3 * j + d] += s->R[j] * o.nxFt[d] - o.Mr[d];",
+     "s->M[3 * j + d] += -s->R[j] * o.nxFt[d] - o.Mr[d];",
+     ["test_angular_momentum_changes_only_by_the_overlap_lever"]),
+    ("rolling torque on j not opposite", "s->M[3 * j + d] += s->R[j] * o.nxFt[d] - o.Mr[d];",
+     "s->M[3 * j + d] += s->R[j] * o.nxFt[d] + o.Mr[d];",
+     ["test_angular_momentum_changes_only_by_the_overlap_lever"]),
+    ("overlap dropped at a search", "for (int d = 0; d < 3; d++) H[3 * k + d] = s->H[3 * a + d];",
+     "for (int d = 0; d < 3; d++) H[3 * k + d] = 0.0;", ["test_trajectory_is_independent_of_the_search_cadence"]),
+    ("search trigger at the full skin", "double half = 0.5 * s->cfg.skin;", "double half = 1.0 * s->cfg.skin;",
+     ["test_trajectory_is_independent_of_the_search_cadence", "test_dynamic_rebuild_keeps_all_contacts_in_list"]),
+    ("particles never leave",
+     "    for (int d = 0; d < 3; d++) s->x[3 * i + d] = s->x[3 * i + d] + s->v[3 * i + d] * c->dt;\n"
+     "    if (s->x[3 * i + 2] < c->z_sink) s->active[i] = 0;",
+     "    for (int d = 0; d < 3; d++) s->x[3 * i + d] = s->x[3 * i + d] + s->v[3 * i + d] * c->dt;\n",
+     ["test_particles_leave_below_z_sink_and_stay_put"]),
     # the paper's variants (pins in test_oracle_variants.py)
     ("linear stiffness exponent", "kn = 16.0 / 15.0 * sR * Ye * fifth_root(arg);",
      "kn = 16.0 / 15.0 * sR * Ye * sqrt(arg);",

@@ -17,7 +17,10 @@ a sign, a lever arm, an inertia factor, a mixing rule) fails at least one of the
   floating wall ........ support until t_off, free fall after
   Coulomb .............. |F_t| <= mu |F_n| always; sliding at 65 deg, sticking at 5 deg;
                          no jump of F_t at the stick-slip switch (Sec. 2.1)
-  momentum, energy ..... pair forces are equal and opposite; e = 1, mu = 0 conserves energy
+  momentum, energy ..... pair forces are equal and opposite; e = 1, mu = 0 conserves energy;
+                         angular momentum changes only by the overlap lever (torque signs on i and j)
+  search cadence ....... thin skin, thick skin and a search every step give the same bits
+  z_sink ............... a falling sphere leaves at the step free fall predicts and stays put
   integrator order ..... 2 for a smooth conservative contact oscillation
   contact search ....... cell list == O(n^2) brute force (NumPy), including r = r_c +- 1 ulp
 """
@@ -571,3 +574,76 @@ def test_history_round_trip_resumes_identically():
     # restarting from full-step velocities recomputes the forces at v^n instead of
     # v^{n-1/2}: the trajectories agree closely but not bitwise
     assert np.abs(xa - xb).max() < 1e-6
+
+
+def test_angular_momentum_changes_only_by_the_overlap_lever():
+    # Pair forces act along the centre line except F_t, whose torques R_i n x F_t and
+    # R_j n x F_t act at the two surfaces; the rolling torques are +M_r and -M_r.  The total
+    # L = sum m x x v + I w therefore changes only by delta_n n x F_t per contact (lever of
+    # the overlap; velocity Verlet adds nothing for central forces), a fraction ~delta_n/R
+    # of the spin changes.  A reversed or halved torque on either side changes L by a
+    # fraction of order one of the tangential or rolling angular impulse.
+    wl = workloads.lattice(n=343, seed=7, walls=False, gravity=(0, 0, 0), speed=0.2)
+    wl.cfg["domain_lo"] = (-0.01, -0.01, -0.01)
+    wl.cfg["domain_hi"] = (0.04, 0.04, 0.04)
+    for m_ in (wl.cfg["particle"], wl.cfg["wall"]):
+        m_["young"] = 1e8                  # small overlaps: a short lever
+    wl.cfg["dt"] = 4e-6
+    R = wl.radius.astype(float)
+    m = 2500.0 * 4.0 / 3.0 * math.pi * R ** 3
+    inertia = 0.4 * m * R ** 2
+
+    def ang(x, v, w):
+        return (m[:, None] * np.cross(x, v)).sum(0) + (inertia[:, None] * w).sum(0)
+
+    s = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius)
+    L0 = ang(wl.x, wl.v, wl.w)
+    s.step(1)
+    assert s.stats()["n_touch"] > 100
+    s.step(749)
+    x, v, w, _ = s.state()
+    spin_change = np.linalg.norm(inertia[:, None] * (w - wl.w), axis=1).sum()
+    assert np.linalg.norm(ang(x, v, w) - L0) < 3e-3 * spin_change
+
+
+def test_trajectory_is_independent_of_the_search_cadence():
+    # A pair enters the force sum only while it touches, in list order (i < j, sorted), and
+    # its tangential overlap survives a search; so a dynamic search with a thin or a thick
+    # skin and a search at every step must give the same bits.  A lost overlap, or a
+    # search that fires too late and misses a contact, breaks the equality.
+    def run(**kw):
+        wl = workloads.lattice(n=343, seed=21, spacing=1.0, speed=0.3)
+        wl.cfg.update(kw)
+        s = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls)
+        s.step(3000)
+        x, v, w, act = s.state()
+        st = s.stats()
+        s.close()
+        return x.tobytes() + v.tobytes() + w.tobytes() + act.tobytes(), st
+
+    thin, s_thin = run(skin=0.1 * 3e-3)
+    thick, s_thick = run(skin=0.4 * 3e-3)
+    every, s_every = run(skin=0.0, neighbor_factor=1.05, rebuild_every=1)
+    assert s_every["rebuilds"] > s_thin["rebuilds"] > s_thick["rebuilds"] > 2
+    assert s_thin["n_touch"] > 20
+    assert thin == thick == every
+
+
+def test_particles_leave_below_z_sink_and_stay_put():
+    # Free fall is exact under velocity Verlet, z_n = z0 - g (n dt)^2 / 2, so the step at
+    # which the centre first drops below z_sink is known; z_sink sits halfway between the
+    # heights of that step and the one before, far from any rounding.
+    dt, z0 = 1e-5, 0.05
+    n_star = 1500
+    z_before = z0 - 0.5 * G * ((n_star - 1) * dt) ** 2
+    z_at = z0 - 0.5 * G * (n_star * dt) ** 2
+    c = cfg(dt=dt, z_sink=0.5 * (z_before + z_at))
+    s = sim1(c, (0.0, 0.0, z0))
+    s.step(n_star - 1)
+    assert s.state()[3][0] == 1
+    s.step(1)
+    x, _, _, act = s.state()
+    assert act[0] == 0 and abs(x[0, 2] - z_at) < 1e-12
+    s.step(200)
+    x2, _, _, act2 = s.state()
+    assert act2[0] == 0 and np.array_equal(x2, x)
