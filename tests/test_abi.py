@@ -144,3 +144,21 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "dem_oracle" not in text, f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no silent fallback: without the compiled library the binding refuses to run
+    monkeypatch.setattr(B, "LIB", str(tmp_path / "absent" / "libdem_gb300.so"))
+    monkeypatch.setattr(D, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        D.load_library(build_if_missing=False)
+
+
+def test_no_cpu_path_without_a_device():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import workloads
+    wl = workloads.lattice(n=64, seed=1)
+    with pytest.raises(RuntimeError):
+        D.DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="fp64")
