@@ -85,6 +85,10 @@ MUTANTS = [
      "    if (s->x[3 * i + 2] < c->z_sink) s->active[i] = 0;",
      "    for (int d = 0; d < 3; d++) s->x[3 * i + d] = s->x[3 * i + d] + s->v[3 * i + d] * c->dt;\n",
      ["test_particles_leave_below_z_sink_and_stay_put"]),
+    ("removed particles still interact", "    if (!s->active[i] || !s->active[j]) {", "    if (0) {",
+     ["test_a_removed_particle_exerts_no_force"]),
+    ("constant search one step late", "return s->since_search >= s->cfg.rebuild_every;",
+     "return s->since_search > s->cfg.rebuild_every;", [("test_constant_search_runs_every_n_steps", dict(every=7))]),
     # the paper's variants (pins in test_oracle_variants.py)
     ("linear stiffness exponent", "kn = 16.0 / 15.0 * sR * Ye * fifth_root(arg);",
      "kn = 16.0 / 15.0 * sR * Ye * sqrt(arg);",

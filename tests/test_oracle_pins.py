@@ -20,7 +20,9 @@ a sign, a lever arm, an inertia factor, a mixing rule) fails at least one of the
   momentum, energy ..... pair forces are equal and opposite; e = 1, mu = 0 conserves energy;
                          angular momentum changes only by the overlap lever (torque signs on i and j)
   search cadence ....... thin skin, thick skin and a search every step give the same bits
-  z_sink ............... a falling sphere leaves at the step free fall predicts and stays put
+  z_sink ............... a falling sphere leaves at the step free fall predicts and stays put;
+                         a removed sphere exerts no force
+  constant search ...... a search before the first step, then one every n steps (Sec. 3.1)
   integrator order ..... 2 for a smooth conservative contact oscillation
   contact search ....... cell list == O(n^2) brute force (NumPy), including r = r_c +- 1 ulp
 """
@@ -647,3 +649,36 @@ def test_particles_leave_below_z_sink_and_stay_put():
     s.step(200)
     x2, _, _, act2 = s.state()
     assert act2[0] == 0 and np.array_equal(x2, x)
+
+
+def test_a_removed_particle_exerts_no_force():
+    # A sits just above z_sink and leaves at the first drift; B starts 0.1 d above contact
+    # with A, in A's fine-search list (skin 0.5 d), and falls through the place where A was
+    # frozen before it has moved far enough to trigger a new search: B's fall stays the
+    # exact free fall, whereas a pair term for the removed A would throw B back up.
+    R = f32(1.5e-3)
+    d = 2 * R
+    dt = 1e-5
+    zA = 0.0
+    c = cfg(dt=dt, z_sink=zA - 1e-12, skin=0.5 * d)
+    x = np.array([[0.0, 0.0, zA], [0.0, 0.0, zA + 1.1 * d]])
+    s = oracle.OracleSim(c, x, np.zeros((2, 3)), np.zeros((2, 3)), np.array([R, R], np.float32))
+    assert s.pairs().tolist() == [[0, 1]]
+    steps = 1000                      # B falls 4.9e-4 m: past A's top, less than skin / 2
+    s.step(steps)
+    xs, _, _, act = s.state()
+    t = steps * dt
+    assert act.tolist() == [0, 1]
+    assert xs[1, 2] < xs[0, 2] + 0.95 * d                      # B has reached A's place
+    assert abs(xs[1, 2] - (zA + 1.1 * d - 0.5 * G * t * t)) < 1e-12
+    assert s.stats()["rebuilds"] == 1
+
+
+@pytest.mark.parametrize("every", [1, 7, 50])
+def test_constant_search_runs_every_n_steps(every):
+    # Sec. 3.1's constant mode: a search before the first step, then one every n steps
+    wl = workloads.lattice(n=125, seed=2, spacing=1.0, speed=0.3)
+    wl.cfg.update(skin=0.0, neighbor_factor=1.3, rebuild_every=every)
+    s = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls)
+    s.step(349)
+    assert s.stats()["rebuilds"] == 1 + 349 // every
