@@ -232,6 +232,24 @@ def find_pairs_static(x, cutoff: float, domain_lo, domain_hi, active=None, capac
     return out[: cnt.value]
 
 
+def history_arrays(pairs, dt_pair, dt_wall, n: int, n_walls: int):
+    """Host arrays for dem_set_history, checked against the shapes the call reads: pairs
+    [k][2] int32 of particle indices, dt_pair [k][3] and dt_wall [n][n_walls][3] float64."""
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    dt_pair = np.ascontiguousarray(dt_pair, dtype=np.float64)
+    if dt_pair.size != 3 * len(pairs):
+        raise ValueError(f"dt_pair holds {dt_pair.size} values for {len(pairs)} pairs (3 per pair)")
+    dt_pair = dt_pair.reshape(-1, 3)
+    if len(pairs) and (pairs.min() < 0 or pairs.max() >= n):
+        raise ValueError(f"pair indices outside [0, {n})")
+    dtw = None
+    if dt_wall is not None:
+        dtw = np.ascontiguousarray(dt_wall, dtype=np.float64)
+        if dtw.shape != (n, n_walls, 3):
+            raise ValueError(f"dt_wall has shape {dtw.shape}, expected {(n, n_walls, 3)}")
+    return pairs, dt_pair, dtw
+
+
 def _host(a, dtype, shape):
     a = np.ascontiguousarray(a, dtype=dtype)
     return a.reshape(shape)
@@ -362,9 +380,7 @@ class DEM:
         return pairs[o], vals[o], dtw[:, : self.n_walls]
 
     def set_history(self, pairs, dt_pair, dt_wall=None):
-        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
-        dt_pair = np.ascontiguousarray(dt_pair, dtype=np.float64).reshape(-1, 3)
-        dtw = None if dt_wall is None else np.ascontiguousarray(dt_wall, dtype=np.float64)
+        pairs, dt_pair, dtw = history_arrays(pairs, dt_pair, dt_wall, self.n, self.n_walls)
         _check(self.lib, "dem_set_history",
                self.lib.dem_set_history(self.h, len(pairs), _ptr(pairs), _ptr(dt_pair), _ptr(dtw)))
 

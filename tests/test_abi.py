@@ -162,3 +162,16 @@ def test_no_cpu_path_without_a_device():
     wl = workloads.lattice(n=64, seed=1)
     with pytest.raises(RuntimeError):
         D.DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="fp64")
+
+
+def test_history_arrays_are_checked_against_the_shapes_the_call_reads():
+    import numpy as np
+    pairs, dtp, dtw = D.history_arrays([[0, 1], [2, 3]], np.zeros(6), np.zeros((4, 2, 3)), 4, 2)
+    assert pairs.dtype == np.int32 and pairs.shape == (2, 2) and dtp.shape == (2, 3) and dtw.shape == (4, 2, 3)
+    assert D.history_arrays(np.zeros((0, 2)), np.zeros((0, 3)), None, 4, 0)[2] is None
+    with pytest.raises(ValueError):
+        D.history_arrays([[0, 1], [2, 3]], np.zeros((1, 3)), None, 4, 0)      # too few values
+    with pytest.raises(ValueError):
+        D.history_arrays([[0, 4]], np.zeros((1, 3)), None, 4, 0)              # index out of range
+    with pytest.raises(ValueError):
+        D.history_arrays([[0, 1]], np.zeros((1, 3)), np.zeros((4, 3)), 4, 1)  # wall array shape
