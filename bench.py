@@ -423,6 +423,7 @@ def run_ours(args):
         w_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
         a_h = torch.empty((n,), dtype=torch.uint8, pin_memory=True)
         g.state((x_h, v_h, w_h, a_h))
+        st_pre = g.stats()
         barrier(world)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -437,6 +438,10 @@ def run_ours(args):
         bytes_io = n * (3 * 3 * 8 + 1)
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": bytes_io / args.steps,
                "d2h_bytes_per_step": bytes_io / args.steps, "steps_per_call": args.steps,
+               # a later window of the same run: its searches and refreshes differ from the
+               # device-timed window's (set_state forces one search)
+               "rebuilds_in_window": st3["rebuilds"] - st_pre["rebuilds"],
+               "inner_builds_in_window": st3["inner_builds"] - st_pre["inner_builds"],
                "note": "dem_set_state(host) + dem_step(steps) + dem_get_state(host), pinned host memory"}
     g.close()
     del g
