@@ -72,10 +72,13 @@ MUTANTS = [
      ["test_annulus_face_and_rim_contact_geometry"]),
     ("tangential torque on j reversed", "s->M[3 * j + d] += s->R[j] * o.nxFt[d] - o.Mr[d];",
      "s->M[3 * j + d] += -s->R[j] * o.nxFt[d] - o.Mr[d];",
-     ["test_angular_momentum_changes_only_by_the_overlap_lever"]),
+     [("test_angular_momentum_changes_only_by_the_overlap_lever", dict(poly=0.0))]),
     ("rolling torque on j not opposite", "s->M[3 * j + d] += s->R[j] * o.nxFt[d] - o.Mr[d];",
      "s->M[3 * j + d] += s->R[j] * o.nxFt[d] + o.Mr[d];",
-     ["test_angular_momentum_changes_only_by_the_overlap_lever"]),
+     [("test_angular_momentum_changes_only_by_the_overlap_lever", dict(poly=0.0))]),
+    ("lever of j taken from i", "s->M[3 * j + d] += s->R[j] * o.nxFt[d] - o.Mr[d];",
+     "s->M[3 * j + d] += s->R[i] * o.nxFt[d] - o.Mr[d];",
+     [("test_angular_momentum_changes_only_by_the_overlap_lever", dict(poly=0.3))]),
     ("overlap dropped at a search", "for (int d = 0; d < 3; d++) H[3 * k + d] = s->H[3 * a + d];",
      "for (int d = 0; d < 3; d++) H[3 * k + d] = 0.0;", ["test_trajectory_is_independent_of_the_search_cadence"]),
     ("search trigger at the full skin", "double half = 0.5 * s->cfg.skin;", "double half = 1.0 * s->cfg.skin;",

@@ -578,14 +578,16 @@ def test_history_round_trip_resumes_identically():
     assert np.abs(xa - xb).max() < 1e-6
 
 
-def test_angular_momentum_changes_only_by_the_overlap_lever():
+@pytest.mark.parametrize("poly", [0.0, 0.3])
+def test_angular_momentum_changes_only_by_the_overlap_lever(poly):
     # Pair forces act along the centre line except F_t, whose torques R_i n x F_t and
     # R_j n x F_t act at the two surfaces; the rolling torques are +M_r and -M_r.  The total
     # L = sum m x x v + I w therefore changes only by delta_n n x F_t per contact (lever of
     # the overlap; velocity Verlet adds nothing for central forces), a fraction ~delta_n/R
     # of the spin changes.  A reversed or halved torque on either side changes L by a
-    # fraction of order one of the tangential or rolling angular impulse.
-    wl = workloads.lattice(n=343, seed=7, walls=False, gravity=(0, 0, 0), speed=0.2)
+    # fraction of order one of the tangential or rolling angular impulse; with unequal
+    # radii, so does a lever taken from the wrong sphere.
+    wl = workloads.lattice(n=343, seed=7, walls=False, gravity=(0, 0, 0), speed=0.2, poly=poly)
     wl.cfg["domain_lo"] = (-0.01, -0.01, -0.01)
     wl.cfg["domain_hi"] = (0.04, 0.04, 0.04)
     for m_ in (wl.cfg["particle"], wl.cfg["wall"]):
@@ -601,10 +603,12 @@ def test_angular_momentum_changes_only_by_the_overlap_lever():
     s = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius)
     L0 = ang(wl.x, wl.v, wl.w)
     s.step(1)
-    assert s.stats()["n_touch"] > 100
+    if poly == 0.0:
+        assert s.stats()["n_touch"] > 100        # a touching lattice
     s.step(749)
     x, v, w, _ = s.state()
     spin_change = np.linalg.norm(inertia[:, None] * (w - wl.w), axis=1).sum()
+    assert spin_change > 0.5 * np.linalg.norm(inertia[:, None] * wl.w, axis=1).sum()   # torques acted
     assert np.linalg.norm(ang(x, v, w) - L0) < 3e-3 * spin_change
 
 
