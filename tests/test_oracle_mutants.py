@@ -79,6 +79,16 @@ MUTANTS = [
     ("lever of j taken from i", "s->M[3 * j + d] += s->R[j] * o.nxFt[d] - o.Mr[d];",
      "s->M[3 * j + d] += s->R[i] * o.nxFt[d] - o.Mr[d];",
      [("test_angular_momentum_changes_only_by_the_overlap_lever", dict(poly=0.3))]),
+    ("wall effective mass halved", "contact_law(nrm, dn, vij, dw, vom, s->R[i], s->m[i], Yw,",
+     "contact_law(nrm, dn, vij, dw, vom, s->R[i], 0.5 * s->m[i], Yw,", ["test_restitution_on_wall"]),
+    ("wall damping from the particle's restitution", "double bw = damping_beta(c->wall.restitution);",
+     "double bw = damping_beta(c->particle.restitution);", ["test_restitution_on_wall"]),
+    ("wall friction from the particle material", "Yw, Gw, bw, c->wall.mu_slide, c->wall.mu_roll,",
+     "Yw, Gw, bw, c->particle.mu_slide, c->wall.mu_roll,", ["test_sliding_then_rolling_five_sevenths"]),
+    ("wall rolling friction from the particle material", "Yw, Gw, bw, c->wall.mu_slide, c->wall.mu_roll,",
+     "Yw, Gw, bw, c->wall.mu_slide, c->particle.mu_roll,", ["test_rolling_resistance_deceleration"]),
+    ("wall shear modulus without the wall", "double Gw = eff_shear(&c->particle, &c->wall);",
+     "double Gw = eff_shear(&c->particle, &c->particle);", ["test_tangential_stiffness_mindlin_with_rolling_coupling"]),
     ("overlap dropped at a search", "for (int d = 0; d < 3; d++) H[3 * k + d] = s->H[3 * a + d];",
      "for (int d = 0; d < 3; d++) H[3 * k + d] = 0.0;", ["test_trajectory_is_independent_of_the_search_cadence"]),
     ("search trigger at the full skin", "double half = 0.5 * s->cfg.skin;", "double half = 1.0 * s->cfg.skin;",

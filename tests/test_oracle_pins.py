@@ -242,7 +242,8 @@ def test_sliding_then_rolling_five_sevenths():
     mu = 0.3
     wm = mat(restitution=0.5, mu_slide=mu, mu_roll=0.0)
     R = f32(1.5e-3)
-    c = cfg(wall=wm, particle=mat(restitution=0.5), dt=2e-6, rolling_model=0)
+    # the particle material's own friction differs: against a wall the wall's mu applies (R8)
+    c = cfg(wall=wm, particle=mat(restitution=0.5, mu_slide=0.7), dt=2e-6, rolling_model=0)
     K = 4.0 / 3.0 * estar(c["particle"], wm) * math.sqrt(R)
     d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
     v0 = 0.2
