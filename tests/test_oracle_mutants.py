@@ -89,6 +89,45 @@ MUTANTS = [
      "Yw, Gw, bw, c->wall.mu_slide, c->particle.mu_roll,", ["test_rolling_resistance_deceleration"]),
     ("wall shear modulus without the wall", "double Gw = eff_shear(&c->particle, &c->wall);",
      "double Gw = eff_shear(&c->particle, &c->particle);", ["test_tangential_stiffness_mindlin_with_rolling_coupling"]),
+    ("partner spin subtracted in the pair contact velocity",
+     "rw[d] = s->R[i] * s->w[3 * i + d] + s->R[j] * s->w[3 * j + d];",
+     "rw[d] = s->R[i] * s->w[3 * i + d] - s->R[j] * s->w[3 * j + d];",
+     ["test_meshing_spins_do_not_slip_and_feel_only_rolling_resistance",
+      "test_sliding_collision_tangential_impulse_is_mu_times_normal"]),
+    ("rotation term of the pair contact velocity reversed", "vij[d] = (s->v[3 * i + d] - s->v[3 * j + d]) + rwxn[d];",
+     "vij[d] = (s->v[3 * i + d] - s->v[3 * j + d]) - rwxn[d];",
+     ["test_sliding_collision_tangential_impulse_is_mu_times_normal"]),
+    ("relative spin of a pair summed", "dw[d] = s->w[3 * i + d] - s->w[3 * j + d];",
+     "dw[d] = s->w[3 * i + d] + s->w[3 * j + d];",
+     ["test_meshing_spins_do_not_slip_and_feel_only_rolling_resistance"]),
+    ("error scales never cleared", "memset(s->Fabs, 0, sizeof(double) * n);", "memset(s->Fabs, 0, 0);",
+     ["test_error_scales_of_a_sliding_sphere"]),
+    ("error scale without the rolling torque", "s->Mabs[i] += s->R[i] * norm3(o.nxFt) + norm3(o.Mr);",
+     "s->Mabs[i] += s->R[i] * norm3(o.nxFt);", ["test_error_scales_of_a_sliding_sphere"]),
+    ("wall overlaps of different particles share a slot", "double* H = &s->Hw[(i * ORC_MAX_WALLS + k) * 3];",
+     "double* H = &s->Hw[(i / ORC_MAX_WALLS + k) * 3];", ["test_spheres_that_never_meet_move_as_if_alone"]),
+    ("rotation origin of a translating wall left behind", "Wt.rot_origin[d] = Wt.rot_origin[d] + Wt.velocity[d] * t;",
+     "Wt.rot_origin[d] = Wt.rot_origin[d] - Wt.velocity[d] * t;", ["test_translating_turntable_carries_a_co_moving_sphere"]),
+    ("floating wall still there at t_off", "t >= W->t_on && t < W->t_off;", "t >= W->t_on && t <= W->t_off;",
+     ["test_floating_wall_window_is_half_open"]),
+    ("floating wall late by a step", "t >= W->t_on && t < W->t_off;", "t > W->t_on && t < W->t_off;",
+     ["test_floating_wall_window_is_half_open"]),
+    ("cylinder axis point added", "if (W->kind == 1) { /* inside of a cylinder: distance to the mantle */\n"
+     "    double rel[3] = {x[0] - W->point[0],", "if (W->kind == 1) { /* inside of a cylinder: distance to the mantle */\n"
+     "    double rel[3] = {x[0] + W->point[0],", ["test_wall_contacts_are_invariant_under_translation"]),
+    ("cylinder radial vector keeps the axial part",
+     "double rad[3] = {rel[0] - ax * W->normal[0], rel[1] - ax * W->normal[1],",
+     "double rad[3] = {rel[0] - ax * W->normal[0], rel[1] + ax * W->normal[1],",
+     ["test_wall_contacts_are_invariant_under_translation"]),
+    ("annulus centre added", "/* annulus: nearest point of a flat ring (face, or the rim of the hole) */\n"
+     "    double rel[3] = {x[0] - W->point[0],", "/* annulus: nearest point of a flat ring (face, or the rim of the hole) */\n"
+     "    double rel[3] = {x[0] + W->point[0],", ["test_wall_contacts_are_invariant_under_translation"]),
+    ("Euler spin update reversed", "s->w[3 * i + d] = s->w[3 * i + d] + al * c->dt;",
+     "s->w[3 * i + d] = s->w[3 * i + d] - al * c->dt;",
+     ["variants.test_explicit_euler_sliding_then_rolling_five_sevenths"]),
+    ("Euler never removes particles", "      s->w[3 * i + d] = s->w[3 * i + d] + al * c->dt;\n    }\n"
+     "    if (s->x[3 * i + 2] < c->z_sink) s->active[i] = 0;", "      s->w[3 * i + d] = s->w[3 * i + d] + al * c->dt;\n    }\n",
+     ["variants.test_explicit_euler_removes_a_sphere_below_z_sink"]),
     ("overlap dropped at a search", "for (int d = 0; d < 3; d++) H[3 * k + d] = s->H[3 * a + d];",
      "for (int d = 0; d < 3; d++) H[3 * k + d] = 0.0;", ["test_trajectory_is_independent_of_the_search_cadence"]),
     ("search trigger at the full skin", "double half = 0.5 * s->cfg.skin;", "double half = 1.0 * s->cfg.skin;",

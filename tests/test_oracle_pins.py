@@ -23,6 +23,12 @@ a sign, a lever arm, an inertia factor, a mixing rule) fails at least one of the
   z_sink ............... a falling sphere leaves at the step free fall predicts and stays put;
                          a removed sphere exerts no force
   constant search ...... a search before the first step, then one every n steps (Sec. 3.1)
+  spinning pairs ....... meshing spins do not slip and feel only rolling resistance (exact);
+                         equal spins slide with tangential impulse mu x normal impulse
+  error scales ......... per-particle |F| and |M| sums of a sliding sphere, every evaluation anew
+  invariance ........... wall contacts under translation; spheres that never meet move as if
+                         alone; a translating turntable carries a co-moving sphere
+  floating wall ........ present for t_on <= t < t_off (exact times with dt = 2^-16)
   integrator order ..... 2 for a smooth conservative contact oscillation
   contact search ....... cell list == O(n^2) brute force (NumPy), including r = r_c +- 1 ulp
 """
@@ -687,3 +693,201 @@ def test_constant_search_runs_every_n_steps(every):
     s = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls)
     s.step(349)
     assert s.stats()["rebuilds"] == 1 + 349 // every
+
+
+def spin_collision(w_i, w_j, mu, mu_r, v_rel=1.0, steps_per_tc=2000):
+    """Head-on elastic collision of two equal steel spheres along x, spinning about z with
+    w_i and w_j.  Returns R, m and the velocities and spins before and after."""
+    R = f32(1e-3)
+    m = mat(young=2e11, poisson=0.3, restitution=1.0, mu_slide=mu, mu_roll=mu_r)
+    rho = 7850.0
+    me = mass(R, rho) / 2.0
+    K = 4.0 / 3.0 * estar(m, m) * math.sqrt(R / 2.0)
+    dmax = (5.0 * me * v_rel ** 2 / (4.0 * K)) ** 0.4
+    dt = 2.94328 * dmax / v_rel / steps_per_tc
+    gap = 0.5 * v_rel * dt * 10
+    x = np.array([[-R - gap, 0.0, 0.0], [R + gap, 0.0, 0.0]])
+    v = np.array([[0.5 * v_rel, 0, 0], [-0.5 * v_rel, 0, 0]])
+    w = np.array([[0, 0, w_i], [0, 0, w_j]], float)
+    c = cfg(particle=m, wall=m, density=rho, gravity=(0, 0, 0), dt=dt, rolling_model=1,
+            domain_lo=(-0.01, -0.01, -0.01), domain_hi=(0.01, 0.01, 0.01))
+    s = oracle.OracleSim(c, x, v, w, np.array([R, R], np.float32))
+    s.step(3 * steps_per_tc)
+    _, v1, w1, _ = s.state()
+    return R, mass(R, rho), v, w, v1, w1
+
+
+def test_meshing_spins_do_not_slip_and_feel_only_rolling_resistance():
+    # Opposite spins about z: the contact points move together, (R_i w_i + R_j w_j) x n = 0,
+    # so there is no tangential force at all; the constant rolling torque -mu_r R_e |F_n|
+    # w_ij/|w_ij| (w_ij = w_i - w_j) acts on i, its opposite on j.  Every force evaluation
+    # pushes i along -x by |F_n| and turns it by mu_r R_e |F_n|, so over the collision
+    # I dw_i = mu_r R_e m dv_x,i exactly.
+    mu_r = 0.1
+    R, m, v0, w0, v1, w1 = spin_collision(1000.0, -1000.0, 0.3, mu_r)
+    inertia = 0.4 * m * R * R
+    dvx = v1[0, 0] - v0[0, 0]
+    assert abs(dvx + 1.0) < 1e-6                           # elastic: the spheres swap velocities
+    assert np.all(v1[:, 1:] == 0.0)                        # no tangential force
+    dw_i = w1[0, 2] - w0[0, 2]
+    assert abs(dw_i - mu_r * (R / 2) * m * dvx / inertia) < 1e-12 * abs(dw_i)
+    assert abs((w1[1, 2] - w0[1, 2]) + dw_i) < 1e-12 * abs(dw_i)
+
+
+def test_sliding_collision_tangential_impulse_is_mu_times_normal():
+    # Equal spins about z: the contact points slide past each other at 2 R w, fast enough
+    # to keep sliding through the whole collision, so |F_t| = mu |F_n| at every evaluation
+    # and F_t on i opposes the slip (-y).  Hence dv_y,i = mu dv_x,i, dv_y,j = -dv_y,i, and
+    # both spins slow by R mu m |dv_x| / I = 2.5 mu |dv_x| / R (up to the small turn of the
+    # centre line during the collision).
+    mu = 0.3
+    R, m, v0, w0, v1, w1 = spin_collision(2000.0, 2000.0, mu, 0.0)
+    dvx = v1[0, 0] - v0[0, 0]
+    dvy = v1[0, 1] - v0[0, 1]
+    assert dvx < -0.99
+    assert abs(dvy - mu * dvx) < 5e-3 * mu * abs(dvx)
+    assert v1[1, 1] == -v1[0, 1]
+    for k in range(2):
+        assert abs((w1[k, 2] - w0[k, 2]) - 2.5 * mu * dvx / R) < 5e-3 * 2.5 * mu * abs(dvx) / R
+    assert 2 * R * w1[0, 2] + (v1[0, 1] - v1[1, 1]) > 0.0      # still sliding at the end
+
+
+def test_error_scales_of_a_sliding_sphere():
+    # The per-particle error scales (sum of |contact force| and of |contact torque|, used to
+    # normalise the GPU force errors) of a sphere sliding on a floor under the Coulomb
+    # limit with constant rolling resistance: |F| = N sqrt(1 + mu^2) and
+    # |M| = R mu N + mu_r R N with N = m g (R_e = R against a wall), every evaluation anew.
+    mu, mu_r = 0.3, 0.1
+    wm = mat(restitution=0.5, mu_slide=mu, mu_roll=mu_r)
+    R = f32(1.5e-3)
+    c = cfg(wall=wm, particle=mat(restitution=0.5), dt=2e-6, rolling_model=1)
+    K = 4.0 / 3.0 * estar(c["particle"], wm) * math.sqrt(R)
+    d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
+    s = sim1(c, (0, 0, R - d_eq), v=(0.2, 0, 0), w=(0, 5.0, 0), R=R, walls=FLOOR)
+    for _ in range(3):
+        s.step(500)                              # well inside the sliding phase
+        Fa, Ma = s.force_scales()
+        N = mass(R) * G
+        assert abs(Fa[0] - N * math.sqrt(1 + mu * mu)) < 1e-3 * N
+        assert abs(Ma[0] - (R * mu * N + mu_r * R * N)) < 1e-3 * R * N
+
+
+def test_wall_contacts_are_invariant_under_translation():
+    # Moving a wall (its point and rotation origin) and the sphere by the same vector must
+    # not change the contact force or torque: a plane, a spinning drum wall touched away
+    # from the axis origin, and an annulus touched on its face and on its rim.
+    pm = mat(restitution=0.5, mu_roll=0.1)
+    wm = mat(restitution=0.5, young=3e7, mu_roll=0.1)
+    R = f32(2.5e-3)
+    c = cfg(particle=pm, wall=wm, gravity=(0, 0, 0), domain_lo=(-0.2, -0.2, -0.2), domain_hi=(0.2, 0.2, 0.2))
+    Rc = 0.05
+    cases = [
+        (lambda o: [workloads.plane(o, (0, 0, 1))], (0.01, -0.02, 2.3e-3)),
+        (lambda o: [workloads.cylinder(o, (0, 1, 0), Rc, omega=3.0, rot_origin=o, rot_axis=(0, 1, 0))],
+         (0.03, 0.017, -math.sqrt((Rc - R + 2e-4) ** 2 - 0.03 ** 2))),
+        (lambda o: [workloads.annulus(o, (0, 0, 1), 0.5, 0.004)], (0.02, 0.0, 2.4e-3)),
+        (lambda o: [workloads.annulus(o, (0, 0, 1), 0.5, 0.004)], (0.0025, 0.001, 1.5e-3)),
+    ]
+    offset = np.array([0.013, -0.021, 0.034])
+    for make, p in cases:
+        out = []
+        for o in (np.zeros(3), offset):
+            s = sim1(c, tuple(np.array(p) + o), v=(0.1, -0.2, 0.05), w=(3.0, -1.0, 2.0), R=R,
+                     walls=make(tuple(o)))
+            F, M = s.forces()
+            out.append((F[0], M[0]))
+        (F0, M0), (F1, M1) = out
+        assert np.linalg.norm(F0) > 0.0
+        assert np.allclose(F1, F0, rtol=1e-8, atol=1e-8 * np.linalg.norm(F0))
+        assert np.allclose(M1, M0, rtol=1e-8, atol=1e-8 * np.linalg.norm(M0) + 1e-30)
+    # and at rest, away from the axis origin, a still drum wall pushes towards its axis
+    # with the Hertz force of the 0.2 mm overlap (R_e = R: a wall of infinite radius)
+    p = np.array(cases[1][1]) + offset
+    s = sim1(c, tuple(p), R=R, walls=[workloads.cylinder(tuple(offset), (0, 1, 0), Rc)])
+    F, _ = s.forces()
+    radial = np.array([p[0] - offset[0], 0.0, p[2] - offset[2]])
+    K = 4.0 / 3.0 * estar(pm, wm) * math.sqrt(R)
+    expect = -K * 2e-4 ** 1.5 * radial / np.linalg.norm(radial)
+    assert np.allclose(F[0], expect, rtol=1e-6, atol=1e-9 * np.linalg.norm(expect))
+
+
+def test_cell_search_with_an_offset_domain_equals_brute_force():
+    rng = np.random.default_rng(4)
+    n = 1200
+    lo = np.array([-0.013, 0.007, -0.021])
+    L = 0.03
+    x = lo + rng.uniform(0, L, (n, 3))
+    R = rng.uniform(0.5e-3, 1e-3, n).astype(np.float32)
+    rc = 1.3 * 2 * float(R.max())
+    c = cfg(domain_lo=tuple(lo), domain_hi=tuple(lo + L), gravity=(0, 0, 0))
+    s = oracle.OracleSim(c, x, np.zeros((n, 3)), np.zeros((n, 3)), R)
+    assert np.array_equal(s.pairs(), numpy_pairs(x, rc))
+
+
+def test_spheres_that_never_meet_move_as_if_alone():
+    # Superposition: three spheres far apart, each sliding and spinning on the same floor,
+    # follow exactly the trajectories they have alone -- per-particle state, wall contacts
+    # and their tangential overlaps do not leak between particles.
+    R = f32(1.5e-3)
+    c = cfg(wall=mat(restitution=0.5, mu_slide=0.3, mu_roll=0.1), dt=2e-6)
+    K = 4.0 / 3.0 * estar(c["particle"], c["wall"]) * math.sqrt(R)
+    d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
+    x = np.array([[-0.05, 0.0, R - d_eq], [0.0, 0.04, R - d_eq], [0.05, -0.03, R - d_eq]])
+    v = np.array([[0.2, 0.0, 0.0], [0.0, -0.15, 0.0], [0.1, 0.1, 0.0]])
+    w = np.array([[0.0, 30.0, 0.0], [40.0, 0.0, 5.0], [-20.0, 10.0, 0.0]])
+    together = oracle.OracleSim(c, x, v, w, np.full(3, R, np.float32), FLOOR)
+    together.step(3000)
+    xt, vt, wt, _ = together.state()
+    for k in range(3):
+        alone = sim1(c, tuple(x[k]), v=tuple(v[k]), w=tuple(w[k]), R=R, walls=FLOOR)
+        alone.step(3000)
+        xa, va, wa, _ = alone.state()
+        assert np.array_equal(xa[0], xt[k]) and np.array_equal(va[0], vt[k]) and np.array_equal(wa[0], wt[k])
+
+
+def test_translating_turntable_carries_a_co_moving_sphere():
+    # A plate that slides along x at V while spinning about the vertical axis through a
+    # point that moves with it: a sphere resting on the axis with the plate's velocity and
+    # spin has no slip and no relative spin, so it rides along at V without drifting.
+    R = f32(1.5e-3)
+    V, Om = 0.05, 4.0
+    c = cfg(wall=mat(restitution=0.5, mu_slide=0.3, mu_roll=0.1), dt=2e-6)
+    K = 4.0 / 3.0 * estar(c["particle"], c["wall"]) * math.sqrt(R)
+    d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
+    plate = [workloads.plane((0, 0, 0), (0, 0, 1), omega=Om, rot_origin=(0.01, 0, 0), rot_axis=(0, 0, 1),
+                             velocity=(V, 0, 0), translates=1)]
+    s = sim1(c, (0.01, 0.0, R - d_eq), v=(V, 0, 0), w=(0, 0, Om), R=R, walls=plate)
+    steps = 5000
+    s.step(steps)
+    x, v, w, _ = s.state()
+    t = steps * 2e-6
+    # rounding of x against the moving axis leaves a slip of ~1e-9 m/s: drift of ~1e-8 m
+    # (an axis left behind at -V t would drag the sphere sideways by ~Om V t^2 = 2e-5 m)
+    assert abs(x[0, 0] - (0.01 + V * t)) < 1e-8 and abs(x[0, 1]) < 1e-7
+    assert abs(v[0, 0] - V) < 1e-5 and abs(v[0, 1]) < 1e-5
+    assert abs(w[0, 2] - Om) < 1e-6
+
+
+def test_floating_wall_window_is_half_open():
+    # A floating wall acts for t_on <= t < t_off (reading of Sec. 3.6).  dt = 2^-16 s makes
+    # both times exact: a falling sphere meets a wall that appears at t_on under it, and a
+    # sphere resting on a wall that vanishes at t_off is supported one step before and not
+    # at t_off.
+    R = f32(1.5e-3)
+    dt = 2.0 ** -16
+    c = cfg(particle=mat(restitution=0.3), wall=mat(restitution=0.3), dt=dt)
+    appears = [workloads.plane((0, 0, 0), (0, 0, 1), t_on=50 * dt)]
+    s = sim1(c, (0, 0, R - 1e-6), R=R, walls=appears)
+    assert s.forces()[0][0, 2] == 0.0       # t = 0 < t_on
+    s.step(49)
+    assert s.forces()[0][0, 2] == 0.0       # t = 49 dt
+    s.step(1)
+    assert s.forces()[0][0, 2] > 0.0        # t = t_on: present
+    K = 4.0 / 3.0 * estar(c["particle"], c["wall"]) * math.sqrt(R)
+    d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
+    vanishes = [workloads.plane((0, 0, 0), (0, 0, 1), t_off=100 * dt)]
+    s = sim1(c, (0, 0, R - d_eq), R=R, walls=vanishes)
+    s.step(99)
+    assert s.forces()[0][0, 2] > 0.5 * mass(R) * G      # t = 99 dt: holding the sphere
+    s.step(1)
+    assert s.forces()[0][0, 2] == 0.0       # t = t_off: gone

@@ -181,3 +181,38 @@ def test_linear_tangential_stiffness_equals_normal():
     assert len(z) > 6
     T_meas = (z[-1] - z[1]) / ((len(z) - 2) / 2.0)
     assert abs(T_meas - T) / T < 1e-4
+
+
+def test_explicit_euler_sliding_then_rolling_five_sevenths():
+    # The rotational update of the Euler step: a sphere sliding on a floor ends rolling at
+    # 5/7 of its initial speed (first-order scheme: 2e-3 at this step size, as Verlet)
+    mu = 0.3
+    wm = mat(restitution=0.5, mu_slide=mu, mu_roll=0.0)
+    R = f32(1.5e-3)
+    c = cfg(wall=wm, particle=mat(restitution=0.5), dt=2e-6, rolling_model=0, integrator=1)
+    K = 4.0 / 3.0 * estar(c["particle"], wm) * math.sqrt(R)
+    d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
+    v0 = 0.2
+    s = sim1(c, (0, 0, R - d_eq), v=(v0, 0, 0), R=R, walls=FLOOR)
+    s.step(int(3.0 * 2 * v0 / (7 * mu * G) / 2e-6))
+    _, v, w, _ = s.state()
+    assert abs(v[0, 0] - 5.0 / 7.0 * v0) / v0 < 2e-3
+    assert abs(w[0, 1] - v[0, 0] / R) / (v[0, 0] / R) < 2e-3
+
+
+def test_explicit_euler_removes_a_sphere_below_z_sink():
+    # Euler free fall z_n = z0 - g dt^2 n (n - 1) / 2 (exact recursion): the sphere leaves at
+    # the first step whose height is below z_sink, placed halfway between two steps
+    dt, z0 = 1e-4, 0.05
+    n_star = 60
+
+    def z(n):
+        return z0 - G * dt * dt * n * (n - 1) / 2
+
+    c = cfg(dt=dt, integrator=1, z_sink=0.5 * (z(n_star - 1) + z(n_star)))
+    s = sim1(c, (0.0, 0.0, z0))
+    s.step(n_star - 1)
+    assert s.state()[3][0] == 1
+    s.step(1)
+    x, _, _, act = s.state()
+    assert act[0] == 0 and abs(x[0, 2] - z(n_star)) < 1e-12
