@@ -128,6 +128,23 @@ MUTANTS = [
     ("Euler never removes particles", "      s->w[3 * i + d] = s->w[3 * i + d] + al * c->dt;\n    }\n"
      "    if (s->x[3 * i + 2] < c->z_sink) s->active[i] = 0;", "      s->w[3 * i + d] = s->w[3 * i + d] + al * c->dt;\n    }\n",
      ["variants.test_explicit_euler_removes_a_sphere_below_z_sink"]),
+    ("pair velocity components mixed", "vij[d] = (s->v[3 * i + d] - s->v[3 * j + d]) + rwxn[d];",
+     "vij[d] = (s->v[3 * i - d] - s->v[3 * j + d]) + rwxn[d];",
+     ["test_an_oblique_spinning_collision_is_rotation_invariant"]),
+    ("partner spin read from the wrong particle", "rw[d] = s->R[i] * s->w[3 * i + d] + s->R[j] * s->w[3 * j + d];",
+     "rw[d] = s->R[i] * s->w[3 * i + d] + s->R[j] * s->w[3 / j + d];",
+     ["test_an_oblique_spinning_collision_is_rotation_invariant"]),
+    ("plane contact point mirrored", "pstar[d] = x[d] - dist * W->normal[d];", "pstar[d] = x[d] + dist * W->normal[d];",
+     ["test_a_paddle_turning_about_its_contact_point_does_not_drag"]),
+    ("cylinder radial vector with a wrong component", "double rad[3] = {rel[0] - ax * W->normal[0],",
+     "double rad[3] = {rel[0] + ax * W->normal[0],", ["test_wall_contacts_are_rotation_invariant"]),
+    ("annulus in-plane offset with a wrong component",
+     "double q[3] = {rel[0] - h * W->normal[0],", "double q[3] = {rel[0] + h * W->normal[0],",
+     ["test_wall_contacts_are_rotation_invariant"]),
+    ("rotation arm with a wrong component", "ps[1] - W->rot_origin[1]", "ps[1] + W->rot_origin[1]",
+     ["test_wall_contacts_are_rotation_invariant"]),
+    ("pair error scale loses the rolling torque", "s->Mabs[i] += s->R[i] * at + ar;", "s->Mabs[i] += s->R[i] * at - ar;",
+     ["test_meshing_spins_do_not_slip_and_feel_only_rolling_resistance"]),
     ("overlap dropped at a search", "for (int d = 0; d < 3; d++) H[3 * k + d] = s->H[3 * a + d];",
      "for (int d = 0; d < 3; d++) H[3 * k + d] = 0.0;", ["test_trajectory_is_independent_of_the_search_cadence"]),
     ("search trigger at the full skin", "double half = 0.5 * s->cfg.skin;", "double half = 1.0 * s->cfg.skin;",

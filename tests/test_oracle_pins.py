@@ -712,8 +712,11 @@ def spin_collision(w_i, w_j, mu, mu_r, v_rel=1.0, steps_per_tc=2000):
     c = cfg(particle=m, wall=m, density=rho, gravity=(0, 0, 0), dt=dt, rolling_model=1,
             domain_lo=(-0.01, -0.01, -0.01), domain_hi=(0.01, 0.01, 0.01))
     s = oracle.OracleSim(c, x, v, w, np.array([R, R], np.float32))
-    s.step(3 * steps_per_tc)
+    s.step(10 + steps_per_tc // 2)                 # half-way through the contact
+    scales = s.force_scales()
+    s.step(3 * steps_per_tc - 10 - steps_per_tc // 2)
     _, v1, w1, _ = s.state()
+    spin_collision.mid_contact_scales = scales
     return R, mass(R, rho), v, w, v1, w1
 
 
@@ -732,6 +735,10 @@ def test_meshing_spins_do_not_slip_and_feel_only_rolling_resistance():
     dw_i = w1[0, 2] - w0[0, 2]
     assert abs(dw_i - mu_r * (R / 2) * m * dvx / inertia) < 1e-12 * abs(dw_i)
     assert abs((w1[1, 2] - w0[1, 2]) + dw_i) < 1e-12 * abs(dw_i)
+    # the error scales mid-contact: |M| = mu_r R_e |F| on both spheres (no tangential force)
+    Fa, Ma = spin_collision.mid_contact_scales
+    assert Fa[0] > 0.0 and Fa[1] == Fa[0]
+    assert np.allclose(Ma, mu_r * (R / 2) * Fa, rtol=1e-12, atol=0)
 
 
 def test_sliding_collision_tangential_impulse_is_mu_times_normal():
@@ -830,16 +837,22 @@ def test_spheres_that_never_meet_move_as_if_alone():
     # and their tangential overlaps do not leak between particles.
     R = f32(1.5e-3)
     c = cfg(wall=mat(restitution=0.5, mu_slide=0.3, mu_roll=0.1), dt=2e-6)
+    # a tilted floor, so that the tangential overlaps have all three components
+    nrm = np.array([0.3, -0.2, 1.0]) / np.linalg.norm([0.3, -0.2, 1.0])
+    floor = [workloads.plane((0, 0, 0), tuple(nrm))]
+    base = np.array([[-0.05, 0.0, 0.0], [0.0, 0.04, 0.0], [0.05, -0.03, 0.0]])
     K = 4.0 / 3.0 * estar(c["particle"], c["wall"]) * math.sqrt(R)
-    d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
-    x = np.array([[-0.05, 0.0, R - d_eq], [0.0, 0.04, R - d_eq], [0.05, -0.03, R - d_eq]])
+    d_eq = (mass(R) * G * nrm[2] / K) ** (2.0 / 3.0)       # resting overlap on the slope
+    x = base - (base @ nrm)[:, None] * nrm + (R - d_eq) * nrm
     v = np.array([[0.2, 0.0, 0.0], [0.0, -0.15, 0.0], [0.1, 0.1, 0.0]])
+    v = v - (v @ nrm)[:, None] * nrm
     w = np.array([[0.0, 30.0, 0.0], [40.0, 0.0, 5.0], [-20.0, 10.0, 0.0]])
-    together = oracle.OracleSim(c, x, v, w, np.full(3, R, np.float32), FLOOR)
+    together = oracle.OracleSim(c, x, v, w, np.full(3, R, np.float32), floor)
     together.step(3000)
     xt, vt, wt, _ = together.state()
+    assert together.stats()["n_wall_touch"] == 3
     for k in range(3):
-        alone = sim1(c, tuple(x[k]), v=tuple(v[k]), w=tuple(w[k]), R=R, walls=FLOOR)
+        alone = sim1(c, tuple(x[k]), v=tuple(v[k]), w=tuple(w[k]), R=R, walls=floor)
         alone.step(3000)
         xa, va, wa, _ = alone.state()
         assert np.array_equal(xa[0], xt[k]) and np.array_equal(va[0], vt[k]) and np.array_equal(wa[0], wt[k])
@@ -891,3 +904,107 @@ def test_floating_wall_window_is_half_open():
     assert s.forces()[0][0, 2] > 0.5 * mass(R) * G      # t = 99 dt: holding the sphere
     s.step(1)
     assert s.forces()[0][0, 2] == 0.0       # t = t_off: gone
+
+
+def rotation(axis, angle):
+    """Rotation matrix about `axis` (Rodrigues)."""
+    k = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * K @ K
+
+
+Q = rotation((0.3, -0.5, 0.8), 1.1)
+
+
+def test_an_oblique_spinning_collision_is_rotation_invariant():
+    # Rotating the whole system rotates the result: three spheres (a far spectator first,
+    # so the colliding pair is (1, 2)), an oblique collision with spins and sliding
+    # friction, and constant rolling resistance, run as given and rotated by Q.
+    R = f32(1e-3)
+    m = mat(young=2e11, poisson=0.3, restitution=0.7, mu_slide=0.3, mu_roll=0.1)
+    c = cfg(particle=m, wall=m, density=7850.0, gravity=(0, 0, 0), dt=2e-8,
+            domain_lo=(-0.02, -0.02, -0.02), domain_hi=(0.02, 0.02, 0.02))
+    x = np.array([[0.012, -0.011, 0.01], [-1.05e-3, 0.0, 0.0], [1.05e-3, 4e-4, -2e-4]])
+    v = np.array([[0.0, 0.0, 0.0], [0.5, 0.1, -0.05], [-0.5, 0.05, 0.1]])
+    w = np.array([[0.0, 0.0, 0.0], [300.0, -200.0, 500.0], [-100.0, 400.0, 250.0]])
+    out = []
+    for T in (np.eye(3), Q):
+        s = oracle.OracleSim(c, x @ T.T, v @ T.T, w @ T.T, np.full(3, R, np.float32))
+        s.step(1)
+        assert s.stats()["n_touch"] == 0
+        s.step(9999)
+        xs, vs, ws, _ = s.state()
+        out.append((xs, vs, ws))
+    (x0, v0, w0), (x1, v1, w1) = out
+    assert np.abs(v0[1:] - v[1:]).max() > 0.05 and np.abs(w0[1:] - w[1:]).max() > 10.0   # they collided
+    assert np.allclose(x1, x0 @ Q.T, rtol=0, atol=1e-12)
+    assert np.allclose(v1, v0 @ Q.T, rtol=0, atol=1e-9)
+    assert np.allclose(w1, w0 @ Q.T, rtol=0, atol=1e-6)
+
+
+def test_wall_contacts_are_rotation_invariant():
+    # A plane, a drum wall spinning about its axis, and an annulus (face and rim), each
+    # with the sphere and all wall vectors rotated by Q and moved off the origin: the
+    # force and torque rotate with them.
+    pm = mat(restitution=0.5, mu_roll=0.1)
+    wm = mat(restitution=0.5, young=3e7, mu_roll=0.1)
+    R = f32(2.5e-3)
+    c = cfg(particle=pm, wall=wm, gravity=(0, 0, 0), domain_lo=(-0.2, -0.2, -0.2), domain_hi=(0.2, 0.2, 0.2))
+    Rc = 0.05
+    off = np.array([0.013, -0.021, 0.034])
+
+    def walls(T, o):
+        y, z = T @ np.array([0.0, 1.0, 0.0]), T @ np.array([0.0, 0.0, 1.0])
+        o = tuple(o)
+        return [
+            [workloads.plane(o, tuple(z))],
+            [workloads.cylinder(o, tuple(y), Rc, omega=3.0, rot_origin=o, rot_axis=tuple(y))],
+            [workloads.annulus(o, tuple(z), 0.5, 0.004, omega=-2.0, rot_origin=o, rot_axis=tuple(z))],
+            [workloads.annulus(o, tuple(z), 0.5, 0.004)],
+        ]
+
+    spots = [(0.01, -0.02, 2.3e-3), (0.03, 0.017, -math.sqrt((Rc - R + 2e-4) ** 2 - 0.03 ** 2)),
+             (0.02, 0.0, 2.4e-3), (0.0025, 0.001, 1.5e-3)]
+    v, w = np.array([0.1, -0.2, 0.05]), np.array([3.0, -1.0, 2.0])
+    for k, p in enumerate(spots):
+        res = []
+        for T, o in ((np.eye(3), np.zeros(3)), (Q, off)):
+            s = sim1(c, tuple(T @ np.array(p) + o), v=tuple(T @ v), w=tuple(T @ w), R=R, walls=walls(T, o)[k])
+            F, M = s.forces()
+            res.append((F[0], M[0]))
+        (F0, M0), (F1, M1) = res
+        assert np.linalg.norm(F0) > 0.0
+        assert np.allclose(F1, Q @ F0, rtol=0, atol=1e-8 * np.linalg.norm(F0)), k
+        assert np.allclose(M1, Q @ M0, rtol=0, atol=1e-8 * np.linalg.norm(M0) + 1e-30), k
+
+
+def test_sphere_on_the_axis_of_the_orifice_touches_the_whole_rim():
+    # Centred over the hole, every rim point is nearest: whichever the contact takes, its
+    # overlap is R - sqrt(r_in^2 + h^2) and the force has that Hertz magnitude.
+    pm = mat(restitution=1.0)
+    wm = mat(restitution=1.0, young=3e7)
+    R = f32(2.5e-3)
+    r_in, h = 0.002, 1.2e-3
+    # (exactly on the axis: a plate in the xy plane through the origin, so that the in-plane
+    # offset is exactly zero; off the origin or tilted, rounding leaves a spurious offset
+    # whose direction is not in the plate)
+    c = cfg(particle=pm, wall=wm, gravity=(0, 0, 0))
+    s = sim1(c, (0.0, 0.0, h), R=R, walls=[workloads.annulus((0, 0, 0), (0, 0, 1), 0.5, r_in)])
+    F, _ = s.forces()
+    K = 4.0 / 3.0 * estar(pm, wm) * math.sqrt(R)
+    delta = R - math.hypot(r_in, h)
+    assert abs(np.linalg.norm(F[0]) - K * delta ** 1.5) < 1e-9 * K * delta ** 1.5
+    assert abs(F[0, 2] - K * delta ** 1.5 * h / math.hypot(r_in, h)) < 1e-9 * K * delta ** 1.5
+
+
+def test_a_paddle_turning_about_its_contact_point_does_not_drag():
+    # A vertical plate (normal +x) turning about the vertical axis through the point the
+    # sphere touches: the surface does not move there, so a still sphere feels only the
+    # normal force, although the plate spins.
+    R = f32(1.5e-3)
+    c = cfg(gravity=(0, 0, 0))
+    paddle = [workloads.plane((0, 0, 0), (1, 0, 0), omega=5.0, rot_origin=(0, 0, 0), rot_axis=(0, 0, 1))]
+    s = sim1(c, (R - 1e-5, 0.0, 0.0), R=R, walls=paddle)
+    F, M = s.forces()
+    assert F[0, 0] > 0.0 and F[0, 1] == 0.0 and F[0, 2] == 0.0
+    assert np.all(M[0] == 0.0)
