@@ -1008,3 +1008,63 @@ def test_a_paddle_turning_about_its_contact_point_does_not_drag():
     F, M = s.forces()
     assert F[0, 0] > 0.0 and F[0, 1] == 0.0 and F[0, 2] == 0.0
     assert np.all(M[0] == 0.0)
+
+
+def test_restart_from_saved_state_and_overlaps_reproduces_the_forces():
+    # With e = 1 and no rolling resistance the contact law depends only on positions and
+    # tangential overlaps.  A new simulation given a saved state and the saved
+    # particle-particle and particle-wall overlaps reads them back unchanged and, at its
+    # first evaluation (new-1: no overlap increment), finds the forces the original
+    # evaluated last (to rounding: the Coulomb limit is re-applied to the saved overlap).
+    wl = workloads.lattice(n=216, seed=8, spacing=0.995, speed=0.05, spin=5.0)
+    settle = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls)
+    settle.step(3000)                           # a bed resting on the floor and the walls
+    x0, v0, w0, _ = settle.state()
+    p0, h0, hw0 = settle.history()
+    c = dict(wl.cfg, particle=dict(wl.cfg["particle"], restitution=1.0, mu_roll=0.0),
+             wall=dict(wl.cfg["wall"], restitution=1.0, mu_roll=0.0))
+    a = oracle.OracleSim(c, x0, v0, w0, wl.radius, wl.walls)
+    a.set_history(p0, h0, hw0)
+    a.step(50)
+    x, v, w, act = a.state()
+    Fa, Ma = a.forces()
+    scale_f, scale_m = a.force_scales()
+    pairs, dtp, dtw = a.history()
+    assert len(pairs) > 10 and np.count_nonzero(dtw) > 0
+    b = oracle.OracleSim(c, x, v, w, wl.radius, wl.walls)
+    b.set_history(pairs, dtp, dtw)
+    pb, hb, hwb = b.history()                   # (reading them runs the first evaluation)
+    assert np.array_equal(pb, pairs)
+    assert np.allclose(hb, dtp, rtol=1e-12, atol=0) and np.allclose(hwb, dtw, rtol=1e-12, atol=0)
+    Fb, Mb = b.forces()
+    assert np.all(np.linalg.norm(Fb - Fa, axis=1) <= 1e-12 * (scale_f + 1e-30))
+    assert np.all(np.linalg.norm(Mb - Ma, axis=1) <= 1e-12 * (scale_m + 1e-30))
+
+
+def test_forces_of_many_particles_obey_newtons_third_law():
+    # Pair forces only (no walls, no gravity): the forces read back for every particle sum
+    # to zero up to rounding, and so do their moments about the origin up to the lever of
+    # the overlaps.
+    wl = workloads.lattice(n=343, seed=9, walls=False, gravity=(0, 0, 0), speed=0.3, spin=30.0)
+    wl.cfg["domain_lo"] = (-0.01, -0.01, -0.01)
+    wl.cfg["domain_hi"] = (0.04, 0.04, 0.04)
+    s = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius)
+    s.step(5)
+    F, M = s.forces()
+    Fa, _ = s.force_scales()
+    assert s.stats()["n_touch"] > 300
+    assert np.abs(F.sum(axis=0)).max() < 1e-12 * Fa.sum()
+    assert np.count_nonzero(np.linalg.norm(F, axis=1)) > 300
+
+
+def test_set_state_round_trip_and_clock():
+    wl = workloads.lattice(n=64, seed=3)
+    s = oracle.OracleSim(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls)
+    rng = np.random.default_rng(1)
+    x2, v2, w2 = wl.x + 1e-5 * rng.normal(size=wl.x.shape), rng.normal(size=(64, 3)), rng.normal(size=(64, 3))
+    s.set_state(x2, v2, w2)
+    x, v, w, act = s.state()
+    assert np.array_equal(x, x2) and np.array_equal(v, v2) and np.array_equal(w, w2) and act.all()
+    s.step(37)
+    st = s.stats()
+    assert st["steps"] == 37 and st["time"] == 37 * wl.cfg["dt"] and st["n_active"] == 64
