@@ -175,3 +175,22 @@ def test_history_arrays_are_checked_against_the_shapes_the_call_reads():
         D.history_arrays([[0, 4]], np.zeros((1, 3)), None, 4, 0)              # index out of range
     with pytest.raises(ValueError):
         D.history_arrays([[0, 1]], np.zeros((1, 3)), np.zeros((4, 3)), 4, 1)  # wall array shape
+
+
+def test_batch_instances_marshal_as_the_workload_states():
+    import workloads
+    wl = workloads.batched_drums(n_instances=8, n_lo=500, n_hi=600)
+    inst = wl.cfg["instances"]
+    arr = D.make_instances(inst)
+    assert len(arr) == 8
+    for k, I in enumerate(inst):
+        a = arr[k]
+        assert a.first == I["first"] and a.n_walls == 3
+        assert a.particle.mu_slide == I["particle"]["mu_slide"] and a.wall.restitution == I["wall"]["restitution"]
+        assert a.walls[0].kind == 1 and a.walls[0].radius == I["radius"]
+        assert tuple(a.walls[0].point) == tuple(map(float, I["center"])) and a.walls[0].omega == I["omega"]
+        assert a.walls[1].kind == 0 and a.walls[2].kind == 0
+    assert [a.first for a in arr] == sorted(a.first for a in arr)
+    too_many = [dict(inst[0], walls=inst[0]["walls"] * 2)]
+    with pytest.raises(ValueError):
+        D.make_instances(too_many)
