@@ -81,3 +81,16 @@ def test_algorithmic_bytes_per_unit():
 def test_job_rate_on_one_rank():
     # 1,000 units in 250 ms: 4,000 units per second
     assert bench.job_rate(1000.0, 250.0, 1) == pytest.approx(4000.0)
+
+
+def test_clock_summary_reads_nvidia_smi_lines():
+    lines = ["0, 1995, 2070, 1201.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+             "0, 2010, 2070, 1250.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "0, 1500, 2070, 700.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+             "garbage", "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    ck = bench.ClockSampler.summarize(lines)
+    assert ck["sm_mhz"] == 1995.0 and ck["sm_max_mhz"] == 2070.0 and ck["samples"] == 3
+    assert ck["reasons"] == ["sw_power_cap"]
+    hot = bench.ClockSampler.summarize(["0, 1200, 2070, 900, 0x40, Not Active, Active, Not Active, Not Active"])
+    assert hot["reasons"] == ["hw_thermal_slowdown"]
+    assert bench.ClockSampler.summarize([])["sm_mhz"] is None
