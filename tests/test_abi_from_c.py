@@ -102,3 +102,11 @@ def test_c_program_uses_the_boundary(built, tmp_path, compiler, std, ext):
         off += fan_out
     assert got["surr_total"] == off
     assert got["surr_ws"] > 0
+
+
+@pytest.mark.parametrize("compiler,std,ext", [("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")])
+def test_headers_are_strict_c99_and_cpp11(tmp_path, compiler, std, ext):
+    src = tmp_path / f"hdr.{ext}"
+    src.write_text('#include "dem.h"\n#include "surrogate.h"\nint main(void) { return 0; }\n')
+    subprocess.check_call([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", INC, str(src),
+                           "-o", str(tmp_path / f"hdr_{ext}")])
