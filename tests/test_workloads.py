@@ -141,3 +141,18 @@ def test_dam_break_recipe():
     dam = wl.walls[-1]
     assert dam["kind"] == 0 and dam["point"][0] == 0.1 and dam["t_off"] == 0.05
     assert wl.cfg["dt"] == 4e-6
+
+
+def test_instance_workload_is_the_batch_member_alone():
+    wl = workloads.batched_drums(n_instances=8, n_lo=500, n_hi=900)
+    for k in (0, 5, 7):
+        I = wl.cfg["instances"][k]
+        one = workloads.instance_workload(wl, k)
+        lo, n = I["first"], I["n"]
+        assert one.n == n and np.array_equal(one.x, wl.x[lo:lo + n]) and np.array_equal(one.radius, wl.radius[lo:lo + n])
+        assert one.walls == I["walls"] and one.cfg["particle"] == I["particle"] and one.cfg["wall"] == I["wall"]
+        assert "instances" not in one.cfg and "n_instances" not in one.cfg
+        # its own domain holds the whole drum and a search radius around it
+        dlo, dhi = np.array(one.cfg["domain_lo"]), np.array(one.cfg["domain_hi"])
+        assert (one.x - one.radius[:, None] >= dlo).all() and (one.x + one.radius[:, None] <= dhi).all()
+        assert dhi[1] - dlo[1] >= I["length"] and dhi[0] - dlo[0] >= 2 * I["radius"]
