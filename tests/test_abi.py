@@ -194,3 +194,9 @@ def test_batch_instances_marshal_as_the_workload_states():
     too_many = [dict(inst[0], walls=inst[0]["walls"] * 2)]
     with pytest.raises(ValueError):
         D.make_instances(too_many)
+
+
+def test_every_cuda_source_is_built_for_sm_103a():
+    csrc = os.path.join(ROOT, "paper_2106_09576_gb300", "csrc")
+    assert {f for f in os.listdir(csrc) if f.endswith(".cu")} == set(B.SOURCES)
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
