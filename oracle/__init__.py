@@ -128,8 +128,6 @@ def _bind(lib):
     lib.orc_get_stats.argtypes = [P, C.POINTER(Stats)]
     lib.orc_brute_pairs.restype = C.c_int64
     lib.orc_brute_pairs.argtypes = [C.c_int64, P, P, C.c_double, P, C.c_int64]
-    lib.orc_fifth_root.restype = C.c_double
-    lib.orc_fifth_root.argtypes = [C.c_double]
     return lib
 
 
@@ -281,8 +279,3 @@ def brute_pairs(x, rc: float, active=None) -> np.ndarray:
     out = np.empty((max(cnt, 1), 2), dtype=np.int32)
     lib.orc_brute_pairs(n, _ptr(x), _ptr(a), float(rc), _ptr(out), cnt)
     return out[:cnt]
-
-
-def fifth_root(x: float) -> float:
-    """The oracle's x^(1/5) (Newton's method), used by the linear contact model."""
-    return float(_load().orc_fifth_root(float(x)))

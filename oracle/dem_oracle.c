@@ -105,28 +105,6 @@ static double linear_damping_den(double e) {
   return 1.0 + q * q;
 }
 
-/* x^(1/5) for x > 0 by Newton's method on y^5 = x: x is scaled by 32^q into [1, 32)
- * (exact), y_{k+1} = (4 y_k + s / y_k^4) / 5 from y_0 = 2 (above the root of the scaled
- * value, so the iterates decrease monotonically), 12 iterations, then scaled back by 2^q.
- * Used for the exponent 0.2 of Eq. linearkn. */
-static double fifth_root(double x) {
-  if (!(x > 0.0)) return 0.0;
-  int e;
-  double m = frexp(x, &e);       /* x = m 2^e, m in [0.5, 1) */
-  m = m * 2.0;                   /* x = m 2^(e-1), m in [1, 2) */
-  e = e - 1;
-  int q = e >= 0 ? e / 5 : -((-e + 4) / 5);
-  int r = e - 5 * q;             /* 0 <= r < 5 */
-  double sv = ldexp(m, r);       /* x = sv 32^q, sv in [1, 32) */
-  double y = 2.0;
-  for (int k = 0; k < 12; k++) {
-    double y2 = y * y;
-    double y4 = y2 * y2;
-    y = (4.0 * y + sv / y4) / 5.0;
-  }
-  return ldexp(y, q);
-}
-
 /* ------------------------------------------------------------ contact law
  * One contact of particle i with a partner (particle j or a wall), Sec. 2.1.
  *   nrm   : unit normal from i towards the partner (Eq. vecn)
@@ -177,7 +155,7 @@ static void contact_law(const double* nrm, double dn, const double* vij, const d
     /* Eqs. linearkn, linearetan; the tangential constants are the same */
     double sR = sqrt(Re);
     double arg = 15.0 * me * lo->V * lo->V / (16.0 * sR * Ye);
-    kn = 16.0 / 15.0 * sR * Ye * fifth_root(arg);
+    kn = 16.0 / 15.0 * sR * Ye * pow(arg, 0.2);
     eta_n = sqrt(4.0 * me * kn / lo->lin_den);
     kt = kn;
     eta_t = eta_n;
@@ -830,4 +808,3 @@ int64_t orc_brute_pairs(int64_t n, const double* x, const uint8_t* active, doubl
   return c;
 }
 
-double orc_fifth_root(double x) { return fifth_root(x); }

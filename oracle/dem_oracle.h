@@ -92,8 +92,6 @@ int64_t orc_get_history(orc_sim* s, int32_t* pairs, double* dt_pair, int64_t cap
 int orc_set_history(orc_sim* s, int64_t n_pairs, const int32_t* pairs, const double* dt_pair,
                     const double* dt_wall);
 int orc_get_stats(const orc_sim* s, orc_stats* out);
-/* x^(1/5) as used by the linear contact model (exported for its pin). */
-double orc_fifth_root(double x);
 /* O(n^2) reference contact search: all i < j with |x_j - x_i|^2 < rc^2. */
 int64_t orc_brute_pairs(int64_t n, const double* x, const uint8_t* active, double rc,
                         int32_t* pairs, int64_t cap);

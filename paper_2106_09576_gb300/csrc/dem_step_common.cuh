@@ -26,35 +26,13 @@ __device__ __forceinline__ void cross3d(const double* a, const double* b, double
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// x^(1/5) for x > 0 by Newton's method on y^5 = s after the exact scaling x = s 32^q with
-// s in [1, 32): y <- (4 y + s / y^4) / 5 from y = 2, 12 iterations, then y 2^q.  Every
-// operation rounds separately (this file is compiled without FMA contraction for the
-// FP64 kernel), so the result is the same as that of any IEEE statement of the method.
-__device__ __forceinline__ double fifth_root_d(double x) {
-  if (!(x > 0.0)) return 0.0;
-  int e;
-  double m = frexp(x, &e);
-  m = m * 2.0;
-  e = e - 1;
-  const int q = e >= 0 ? e / 5 : -((-e + 4) / 5);
-  const int r = e - 5 * q;
-  const double sv = ldexp(m, r);
-  double y = 2.0;
-  for (int k = 0; k < 12; k++) {
-    const double y2 = y * y;
-    const double y4 = y2 * y2;
-    y = (4.0 * y + sv / y4) / 5.0;
-  }
-  return ldexp(y, q);
-}
-
 // Linear model (Eqs. linearkn, linearetan): k and eta from the pair's R_e, m_e, Y_e and
 // the characteristic impact velocity V; the same constants act tangentially.
 __device__ __forceinline__ void linear_constants_d(double Re, double me, double Ye, double V, double lin_den,
                                                    double* k, double* eta) {
   const double sR = sqrt(Re);
   const double arg = 15.0 * me * V * V / (16.0 * sR * Ye);
-  *k = 16.0 / 15.0 * sR * Ye * fifth_root_d(arg);
+  *k = 16.0 / 15.0 * sR * Ye * pow(arg, 0.2);
   *eta = sqrt(4.0 * me * (*k) / lin_den);
 }
 

@@ -1,7 +1,10 @@
 """The paper's other options on the GPU: the linear contact model, viscous rolling,
 explicit Euler and translating walls.  The FP64 path reproduces the oracle bit for bit
-(same operations in the same order); the mixed path stays within the same tolerance as
-the default model."""
+(same operations in the same order) except for the x^0.2 of Eq. linearkn, which the
+oracle takes from the C library and the kernel from CUDA's pow: both are within 2 ulp of
+the exact power, so with the linear model the FP64 path is held to 1e-12 relative after
+one step, and to bounds on the slow (chaotic) growth of that difference over 200 steps.
+The mixed path stays within the same tolerance as the default model."""
 import numpy as np
 import pytest
 
@@ -27,7 +30,12 @@ def with_variant(wl, **kw):
     return wl
 
 
-@pytest.mark.parametrize("name", list(VARIANTS))
+EXACT_VARIANTS = [k for k, v in VARIANTS.items() if v.get("contact_model", 0) == 0]
+LINEAR_VARIANTS = [k for k, v in VARIANTS.items() if v.get("contact_model", 0) == 1]
+FP64_TOL = 1e-12   # one-step force and position bar of the FP64 path
+
+
+@pytest.mark.parametrize("name", EXACT_VARIANTS)
 def test_variant_fp64_bit_exact_with_rebuilds(name):
     wl = with_variant(dense(n=1500, seed=61, speed=1.0), **VARIANTS[name])
     g, o = make_gpu(wl, "fp64"), make_oracle(wl)
@@ -40,6 +48,48 @@ def test_variant_fp64_bit_exact_with_rebuilds(name):
         o.step(chunk)
         compare_exact(g, o)
     assert g.stats()["rebuilds"] == o.stats()["rebuilds"] >= 2
+
+
+@pytest.mark.parametrize("name", LINEAR_VARIANTS)
+def test_linear_model_fp64_within_1e12_with_rebuilds(name):
+    """Eq. linearkn's x^0.2 differs by at most a few ulp between the C library and CUDA;
+    every other operation is the oracle's.  Bars: forces 1e-12 relative (R19 scale) at the
+    first evaluation and after one step, positions 1e-12 relative to the box; after 201
+    steps, forces 1e-9, velocities 1e-10 of the largest speed and positions 1e-12 d_max
+    (a 1-ulp change of every velocity grows to 4e-11, 5e-13 and 2e-13 d_max in the
+    oracle itself)."""
+    wl = with_variant(dense(n=1500, seed=61, speed=1.0), **VARIANTS[name])
+    g, o = make_gpu(wl, "fp64"), make_oracle(wl)
+    with_history(wl, g, o)
+    m = masses(wl)
+    gvec = wl.cfg["gravity"]
+    dmax = 2.0 * float(wl.radius.max())
+    box = float(np.abs(wl.x).max())
+
+    def ferr():
+        Fg, Mg = g.forces()
+        Fo, Mo = o.forces()
+        Fa, Ma = o.force_scales()
+        return (force_error(Fg, Fo, Fa, m, gvec),
+                torque_error(Mg, Mo, Ma, m, wl.radius.astype(float), gvec))
+
+    ef, em = ferr()
+    assert ef <= FP64_TOL and em <= FP64_TOL
+    for chunk, ftol, vtol, xtol in ((1, FP64_TOL, 1e-12, FP64_TOL * box), (20, 1e-9, 1e-10, 1e-12 * dmax),
+                                    (180, 1e-9, 1e-10, 1e-12 * dmax)):
+        g.step(chunk)
+        o.step(chunk)
+        xg, vg, wg, ag = g.state()
+        xo, vo, wo, ao = o.state()
+        assert np.array_equal(ag, ao)
+        ef, em = ferr()
+        print(f"{name} after +{chunk}: force {ef:.2e} torque {em:.2e} "
+              f"x {np.abs(xg - xo).max():.2e} m v {np.abs(vg - vo).max():.2e} m/s")
+        assert ef <= ftol and em <= ftol
+        assert np.abs(xg - xo).max() <= xtol
+        assert np.abs(vg - vo).max() <= vtol * np.abs(vo).max()
+    assert g.stats()["rebuilds"] == o.stats()["rebuilds"] >= 2
+    assert np.array_equal(g.pairs(), o.pairs())
 
 
 def piston(n=1200, precision="fp64", U=0.05):

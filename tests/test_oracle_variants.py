@@ -3,7 +3,6 @@ the linear contact model (Eqs. linearkn, linearetan), the viscous rolling resist
 (Table rolling_torque), the explicit Euler integrator (Eq. integ_EE) and walls whose
 geometry translates (Sec. 3.6).  Each against a closed form:
 
-  fifth root ........... Newton x^(1/5) against the library power (1e-14) and exact powers
   linear stiffness ..... k_n is the spring that gives Hertz's maximum overlap at impact speed
                          V; a linear spring's contact time pi sqrt(m_e / k_n) is independent
                          of the impact speed and its maximum overlap scales with it
@@ -21,19 +20,6 @@ import pytest
 import oracle
 import workloads
 from test_oracle_pins import FLOOR, G, cfg, crossing_times, estar, f32, mass, mat, sim1
-
-
-@pytest.mark.parametrize("seed", [0, 1])
-def test_fifth_root_matches_the_library_power(seed):
-    rng = np.random.default_rng(seed)
-    xs = np.exp(rng.uniform(math.log(1e-30), math.log(1e30), 2000))
-    for x in xs:
-        got = oracle.fifth_root(float(x))
-        ref = float(x) ** 0.2
-        assert abs(got - ref) <= 1e-14 * ref, (x, got, ref)
-    for k in range(-40, 41):
-        assert oracle.fifth_root(2.0 ** (5 * k)) == 2.0 ** k
-    assert oracle.fifth_root(3125.0) == 5.0 and oracle.fifth_root(0.0) == 0.0
 
 
 def linear_two_sphere(e, v_rel, V, R=float(np.float32(1e-3)), rho=7850.0, young=2e11, nu=0.3, steps=4000):
