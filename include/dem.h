@@ -245,15 +245,20 @@ dem_status dem_get_stats(dem_ctx* ctx, dem_stats* out);
  *   x       device, [n][3] FP64;  active: device uint8 [n] or NULL (all active)
  *   domain  host double[3] each: box of the cell grid (points outside are clamped)
  *   pairs   device int32 [capacity][2]: the first min(count, capacity) pairs, ordered by
- *           i, then by the cells sharing a vertex with i's cell
- *   count   host: total number of pairs (the call synchronises `stream`)
+ *           i, then by the cells sharing a vertex with i's cell, then by j within a cell;
+ *           may be NULL when capacity is 0 (count only)
+ *   count   host: total number of pairs
  * Limits: n <= DEM_STATIC_MAX_PARTICLES (else DEM_ERR_CAPACITY); grids finer than
- * DEM_STATIC_MAX_CELLS cells are coarsened.  All calls share the scratch and it keeps the
- * last call's contents (the per-cell counters are cleared by every call); calls that
- * overlap on the GPU race and must not be issued.  The first call on a device looks up
- * the scratch's device address on that device, so make it before any stream capture. */
+ * DEM_STATIC_MAX_CELLS cells are coarsened; a total above DEM_STATIC_MAX_PAIRS returns
+ * DEM_ERR_CAPACITY with `count` set to the total and nothing written.  The call reads the
+ * total back to the host and synchronises `stream` (twice when pairs are written), so it
+ * cannot be captured into a CUDA graph.  All calls share the scratch and it keeps the
+ * last call's contents (the per-cell counters and the total are cleared by every call);
+ * calls that overlap on the GPU race and must not be issued.  The first call on a device
+ * looks up the scratch's device address on that device, which must be current. */
 #define DEM_STATIC_MAX_PARTICLES 262144
 #define DEM_STATIC_MAX_CELLS 524288
+#define DEM_STATIC_MAX_PAIRS 2147483647
 dem_status dem_find_pairs_static(const double* x, const uint8_t* active, int64_t n, double cutoff,
                                  const double* domain_lo, const double* domain_hi, int32_t* pairs,
                                  int64_t capacity, int64_t* count, void* stream);

@@ -11,15 +11,17 @@
 // on which the library is loaded holds it until the process exits.  It bounds the
 // problem to DEM_STATIC_MAX_PARTICLES particles; grids with more than
 // DEM_STATIC_MAX_CELLS cells are coarsened (cells stay at least as large as the cutoff).
+// The pair total is counted in 64 bits first; a total above DEM_STATIC_MAX_PAIRS is
+// refused before any pair is written, so the 32-bit per-particle offsets never wrap.
 // All calls share the array and it keeps the last call's contents: the per-cell counters
-// are cleared at the start of every call, everything else is overwritten before it is
-// read.  Calls whose work overlaps on the GPU (two streams, or two host threads) race on
-// the array and must not be issued.
+// and the pair total are cleared at the start of every call, everything else is
+// overwritten before it is read.  Calls whose work overlaps on the GPU (two streams, or
+// two host threads) race on the array and must not be issued.
 //
 // Host code cannot use the array's name as a device address: the first call on each
 // device looks the address up with cudaGetSymbolAddress while that device is current,
-// and later calls on that device reuse it.  That first call should therefore happen
-// before any stream capture is begun.
+// and later calls on that device reuse it.  Every call reads the pair total back to the
+// host and synchronises its stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,7 +40,7 @@ constexpr int kMaxDevices = 64;
 __device__ __align__(256) unsigned char g_pair_scratch[kStaticScratchBytes];
 
 struct ScratchLayout {
-  size_t count, start, key, local, order, pcount, poff, partials, total;
+  size_t count, start, key, local, order, pcount, poff, partials, pairs64, total;
 };
 
 constexpr size_t align_up(size_t v) { return (v + kRegionAlign - 1) / kRegionAlign * kRegionAlign; }
@@ -54,6 +56,7 @@ constexpr ScratchLayout make_layout(size_t cells, size_t n) {
   L.pcount = o;   o = align_up(o + n * 4);
   L.poff = o;     o = align_up(o + (n + 1) * 4);
   L.partials = o; o = align_up(o + 4096 * 4);
+  L.pairs64 = o;  o = align_up(o + 8);
   L.total = o;
   return L;
 }
@@ -93,26 +96,29 @@ __global__ void k_sp_scatter(int n, const int* key, const int* local, const int*
   order[start[key[p]] + local[p]] = p;
 }
 
-// each cell in increasing particle index: the output does not depend on atomic order
-__global__ void k_sp_cell_order(int cells, const int* start, int* order) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// Each cell's members in increasing particle index, written to `sorted`: the member at
+// scatter position s (any order, from the atomics of k_sp_key) goes to the cell start plus
+// the number of members with a smaller index.  One thread per particle, so a crowded
+// cell costs each of its m members O(m) work -- the same as the pair search over that
+// cell -- and no thread ever sorts a whole cell.  The out-of-system bucket is not used.
+__global__ void k_sp_rank(int n, int cells, const int* key, const int* start, const int* order, int* sorted) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int p = order[s];
+  const int c = key[p];
   if (c >= cells) return;
   const int b = start[c], e = start[c + 1];
-  for (int a = b + 1; a < e; a++) {
-    const int v = order[a];
-    int k = a - 1;
-    while (k >= b && order[k] > v) {
-      order[k + 1] = order[k];
-      k--;
-    }
-    order[k + 1] = v;
-  }
+  int r = 0;
+  for (int t = b; t < e; t++) r += order[t] < p ? 1 : 0;
+  sorted[b + r] = p;
 }
 
 // Pairs (i, j), i < j, |x_j - x_i|^2 < rc^2 (same rounding as the context's fine search).
-// mode 0: count per i; mode 1: write at off[i].
+// mode 0: count per i, and the 64-bit total; mode 1: write at off[i] (the caller has
+// checked that the total, hence every offset, fits in 32 bits).
 __global__ void k_sp_pairs(const double* x, const uint8_t* active, int n, Grid g, double rc2, const int* start,
-                           const int* order, int* pcount, const int* poff, int* pairs, long long capacity, int mode) {
+                           const int* order, int* pcount, const int* poff, int* pairs, long long capacity, int mode,
+                           unsigned long long* total) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (active && !active[i]) {
@@ -139,7 +145,7 @@ __global__ void k_sp_pairs(const double* x, const uint8_t* active, int n, Grid g
           const double s2 = demgb::sqdist_exact(xi, yi, zi, x[3 * (size_t)j], x[3 * (size_t)j + 1],
                                                 x[3 * (size_t)j + 2]);
           if (!(s2 < rc2)) continue;
-          if (mode == 1 && out < capacity) {
+          if (mode == 1 && out >= 0 && out < capacity) {
             pairs[2 * out] = i;
             pairs[2 * out + 1] = j;
           }
@@ -149,7 +155,12 @@ __global__ void k_sp_pairs(const double* x, const uint8_t* active, int n, Grid g
       }
     }
   }
-  if (mode == 0) pcount[i] = c;
+  if (mode == 0) {
+    pcount[i] = c;
+    const unsigned act = __activemask();
+    const unsigned long long ws = __reduce_add_sync(act, (unsigned)c);
+    if ((threadIdx.x & 31) == __ffs(act) - 1 && ws) atomicAdd(total, ws);
+  }
 }
 
 }  // namespace
@@ -201,24 +212,32 @@ extern "C" dem_status dem_find_pairs_static(const double* x, const uint8_t* acti
   int* pcount = (int*)(base + L.pcount);
   int* poff = (int*)(base + L.poff);
   int* partials = (int*)(base + L.partials);
+  unsigned long long* total64 = (unsigned long long*)(base + L.pairs64);
   cudaStream_t s = (cudaStream_t)stream;
   const int T = 256;
   const int nb = (int)((n + T - 1) / T);
   const double rc2 = cutoff * cutoff;
 
-  if (cudaMemsetAsync(cnt, 0, ((size_t)g.cells + 1) * 4, s) != cudaSuccess) return DEM_ERR_CUDA;
+  if (cudaMemsetAsync(cnt, 0, ((size_t)g.cells + 1) * 4, s) != cudaSuccess ||
+      cudaMemsetAsync(total64, 0, 8, s) != cudaSuccess)
+    return DEM_ERR_CUDA;
   k_sp_key<<<nb, T, 0, s>>>(x, active, (int)n, g, key, local, cnt);
   demgb::scan_exclusive_i32(cnt, g.cells + 1, start, partials, s);
   k_sp_scatter<<<nb, T, 0, s>>>((int)n, key, local, start, order);
-  k_sp_cell_order<<<(g.cells + T - 1) / T, T, 0, s>>>(g.cells, start, order);
-  k_sp_pairs<<<nb, T, 0, s>>>(x, active, (int)n, g, rc2, start, order, pcount, nullptr, nullptr, 0, 0);
-  demgb::scan_exclusive_i32(pcount, (int)n, poff, partials, s);
-  k_sp_pairs<<<nb, T, 0, s>>>(x, active, (int)n, g, rc2, start, order, pcount, poff, pairs, capacity, 1);
-  if (cudaGetLastError() != cudaSuccess) return DEM_ERR_CUDA;
-  int total = 0;
-  if (cudaMemcpyAsync(&total, poff + n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  // `local` is free after the scatter: it receives the cell-ordered members
+  k_sp_rank<<<nb, T, 0, s>>>((int)n, g.cells, key, start, order, local);
+  int* sorted = local;
+  k_sp_pairs<<<nb, T, 0, s>>>(x, active, (int)n, g, rc2, start, sorted, pcount, nullptr, nullptr, 0, 0, total64);
+  unsigned long long total = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&total, total64, sizeof(total), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return DEM_ERR_CUDA;
-  *count = total;
+  *count = (int64_t)total;
+  if (total > (unsigned long long)DEM_STATIC_MAX_PAIRS) return DEM_ERR_CAPACITY;   // nothing written
+  if (capacity == 0) return DEM_OK;
+  demgb::scan_exclusive_i32(pcount, (int)n, poff, partials, s);
+  k_sp_pairs<<<nb, T, 0, s>>>(x, active, (int)n, g, rc2, start, sorted, pcount, poff, pairs, capacity, 1, total64);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return DEM_ERR_CUDA;
   return DEM_OK;
 }

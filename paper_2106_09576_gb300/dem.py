@@ -198,38 +198,54 @@ def make_walls(walls):
     return arr, len(walls)
 
 
-def find_pairs_static(x, cutoff: float, domain_lo, domain_hi, active=None, capacity=None, stream=None):
+def find_pairs_static(x, cutoff: float, domain_lo, domain_hi, active=None, out=None, stream=None):
     """dem_find_pairs_static: contact search without any device allocation by the library.
 
-    For callers that cannot allocate device memory; `x` ([n, 3] float64), `active`
-    ([n] uint8, optional) are CUDA tensors.  Returns a CUDA int32 tensor [count, 2] of the
-    pairs (i < j) with |x_j - x_i| < cutoff.  The output tensor is allocated here by torch
-    on the caller's behalf; C callers pass their own buffer."""
+    For callers that cannot allocate device memory; `x` ([n, 3] float64, contiguous) and
+    `active` ([n] uint8, optional) are CUDA tensors on one device, which is made current
+    for the call.  With `out` (a contiguous CUDA int32 tensor [capacity, 2]) the call
+    writes the first min(count, capacity) pairs into it, allocates nothing, and returns
+    the total count.  Without it, a tensor of exactly count rows is allocated here by
+    torch on the caller's behalf (one counting call, one writing call) and returned."""
     import torch
 
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.dim() == 2
+            and x.shape[1] == 3 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous CUDA float64 tensor of shape [n, 3]")
+    n = int(x.shape[0])
+    if active is not None and not (isinstance(active, torch.Tensor) and active.device == x.device
+                                   and active.dtype == torch.uint8 and active.shape == (n,)
+                                   and active.is_contiguous()):
+        raise ValueError("active must be a contiguous uint8 tensor of shape [n] on x's device")
+    if out is not None and not (isinstance(out, torch.Tensor) and out.device == x.device and out.dtype == torch.int32
+                                and out.dim() == 2 and out.shape[1] == 2 and out.is_contiguous()):
+        raise ValueError("out must be a contiguous int32 tensor of shape [capacity, 2] on x's device")
     lib = load_library()
     f = lib.dem_find_pairs_static
     if f.argtypes is None:
         f.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.POINTER(C.c_double),
                       C.POINTER(C.c_double), C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]
         f.restype = C.c_int32
-    n = int(x.shape[0])
     lo = (C.c_double * 3)(*[float(v) for v in domain_lo])
     hi = (C.c_double * 3)(*[float(v) for v in domain_hi])
-    st = stream if stream is not None else torch.cuda.current_stream(x.device)
-    cnt = C.c_int64(0)
-    cap = int(capacity) if capacity is not None else 0
-    out = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=x.device)
-    a = None if active is None else C.c_void_p(active.data_ptr())
-    _check(lib, "dem_find_pairs_static", f(C.c_void_p(x.data_ptr()), a, n, float(cutoff), lo, hi,
-                                            C.c_void_p(out.data_ptr()), cap, C.byref(cnt),
-                                            C.c_void_p(st.cuda_stream)))
-    if capacity is None or cnt.value > cap:
-        out = torch.empty((max(cnt.value, 1), 2), dtype=torch.int32, device=x.device)
-        _check(lib, "dem_find_pairs_static", f(C.c_void_p(x.data_ptr()), a, n, float(cutoff), lo, hi,
-                                                C.c_void_p(out.data_ptr()), cnt.value, C.byref(cnt),
-                                                C.c_void_p(st.cuda_stream)))
-    return out[: cnt.value]
+    with torch.cuda.device(x.device):
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
+        sp = C.c_void_p(st.cuda_stream)
+        cnt = C.c_int64(0)
+        a = None if active is None else C.c_void_p(active.data_ptr())
+        xp = C.c_void_p(x.data_ptr())
+        if out is not None:
+            cap = int(out.shape[0])
+            _check(lib, "dem_find_pairs_static", f(xp, a, n, float(cutoff), lo, hi,
+                                                    C.c_void_p(out.data_ptr()) if cap else None, cap,
+                                                    C.byref(cnt), sp))
+            return int(cnt.value)
+        _check(lib, "dem_find_pairs_static", f(xp, a, n, float(cutoff), lo, hi, None, 0, C.byref(cnt), sp))
+        res = torch.empty((max(cnt.value, 1), 2), dtype=torch.int32, device=x.device)
+        if cnt.value:
+            _check(lib, "dem_find_pairs_static", f(xp, a, n, float(cutoff), lo, hi, C.c_void_p(res.data_ptr()),
+                                                    cnt.value, C.byref(cnt), sp))
+        return res[: cnt.value]
 
 
 def history_arrays(pairs, dt_pair, dt_wall, n: int, n_walls: int):

@@ -200,3 +200,28 @@ def test_every_cuda_source_is_built_for_sm_103a():
     csrc = os.path.join(ROOT, "paper_2106_09576_gb300", "csrc")
     assert {f for f in os.listdir(csrc) if f.endswith(".cu")} == set(B.SOURCES)
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_static_pair_search_checks_its_tensors_before_any_call():
+    """find_pairs_static refuses tensors the C call would misread (wrong dtype, shape,
+    strides or device) before it touches the library or a device."""
+    import torch
+
+    from paper_2106_09576_gb300.dem import find_pairs_static
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    for bad in (torch.zeros((10, 3), dtype=torch.float64),            # host tensor
+                torch.zeros((10, 3), dtype=torch.float32),
+                torch.zeros((3, 10), dtype=torch.float64).t(),         # strided
+                torch.zeros((10, 4), dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            find_pairs_static(bad, 0.1, lo, hi)
+
+
+def test_static_pair_limits_in_the_header():
+    """The static search's limits: the pair total that the 32-bit offsets can hold, and a
+    scratch layout that fits the advertised particle and cell limits (the library's own
+    static_assert checks the latter at build time)."""
+    txt = open(os.path.join(ROOT, "include", "dem.h")).read()
+    vals = dict(re.findall(r"#define (DEM_STATIC_MAX_\w+) (\d+)", txt))
+    assert int(vals["DEM_STATIC_MAX_PAIRS"]) == 2 ** 31 - 1
+    assert int(vals["DEM_STATIC_MAX_PARTICLES"]) == 262144 and int(vals["DEM_STATIC_MAX_CELLS"]) == 524288
