@@ -62,6 +62,11 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-batched", action="store_true", help="skip the batch of 512 drums")
     p.add_argument("--batched-steps", type=int, default=10000)
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other configurations' lines (cube, drum, silo discharge)")
+    p.add_argument("--pair-eval", choices=["once", "both"], default="once",
+                   help="mixed step: each touching pair evaluated once (its reaction handed to the "
+                        "partner) or from both sides")
     return p.parse_args()
 
 
@@ -161,19 +166,42 @@ def sources_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_desc, n):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def recorded_traffic(kernel, workload_desc, n):
+    """DRAM bytes per step (the step kernels' launches) from the committed ncu summary, if
+    it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     sha = sources_sha()
     for line in open(path):
         f = line.split()
-        if len(f) >= 5 and not line.startswith("#") and f[0] == "k_step_mixed" and f[1] == workload_desc \
+        if len(f) >= 5 and not line.startswith("#") and f[0] == kernel and f[1] == workload_desc \
                 and f[2] == sha:
             per_particle = float(f[3]) / float(f[4])
             return per_particle * n
+    return None
+
+
+FP64_STEP_SOURCES = ["paper_2106_09576_gb300/csrc/dem_step_common.cuh", "paper_2106_09576_gb300/csrc/dem_step_fp64.cu",
+                     "paper_2106_09576_gb300/csrc/dem_device.cuh"]
+
+
+def recorded_pipe_counts(kernel, workload_desc, sources):
+    """FP64-pipe and all warp instructions per particle of one launch of `kernel`, from the
+    committed ncu summary (profiles/pipe_counts.txt), if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "pipe_counts.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for rel in sources:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()[:16]
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 6 and not line.startswith("#") and f[0] == kernel and f[1] == workload_desc and f[2] == sha:
+            n = float(f[5])
+            return {"fp64_warp_inst_per_particle": float(f[3]) / n, "warp_inst_per_particle": float(f[4]) / n}
     return None
 
 
@@ -265,6 +293,78 @@ def oracle_rate(wl, seconds, max_steps=None, warmup=0):
     return s.n * steps / dt, s.n, steps, dt
 
 
+def _spread_centres(x, p, seed=0):
+    """p well-separated sample centres (farthest-point choice on a subsample of x)."""
+    rng = np.random.default_rng(seed)
+    sub = x[rng.choice(len(x), size=min(len(x), 20000), replace=False)]
+    c = [sub[np.argmin(np.linalg.norm(sub - sub.mean(0), axis=1))]]
+    d = np.linalg.norm(sub - c[0], axis=1)
+    while len(c) < p:
+        c.append(sub[int(np.argmax(d))])
+        d = np.minimum(d, np.linalg.norm(sub - c[-1], axis=1))
+    return np.array(c)
+
+
+_BARRIER = None
+
+
+def _pool_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_task(task):
+    """One core's share of the all-core baseline: the oracle on its own sample, first
+    search and force evaluation untimed, then `steps` steps timed from a common start."""
+    cfg, walls, x, v, w, r, steps = task
+    import oracle
+    o = oracle.OracleSim(cfg, x, v, w, r, walls)
+    o.step(1)
+    _BARRIER.wait(timeout=600)
+    t0 = time.monotonic()
+    o.step(steps)
+    t1 = time.monotonic()
+    o.close()
+    return len(x) * steps, t0, t1
+
+
+def oracle_rate_all_cores(wl, seconds, cores):
+    """The oracle on every host core at once: `cores` single-thread processes (spawned, so
+    no CUDA state is inherited), each on a ball of up to n / cores (at most 200,000)
+    spheres around its own well-separated centre of the workload, stepped long enough
+    (from the single-thread speed) for about `seconds`; rate = all particle-steps /
+    (last finish - first start)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import oracle
+    import workloads
+    oracle.build()
+    one, _, _, _ = oracle_rate(wl, 2.0, max_steps=2)
+    k = int(max(min(2000, wl.n), min(wl.n // cores, 200_000)))
+    steps = int(min(200, max(3, one * seconds / k)))
+    tasks = []
+    for c in _spread_centres(wl.x, cores):
+        idx = np.sort(np.argsort(np.linalg.norm(wl.x - c, axis=1), kind="stable")[:k])
+        sw = workloads.Workload("sample", dict(wl.cfg), wl.walls, wl.x[idx], wl.v[idx], wl.w[idx], wl.radius[idx])
+        tasks.append((sw.cfg, sw.walls, sw.x, sw.v, sw.w, sw.radius, steps))
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    with ProcessPoolExecutor(max_workers=cores, mp_context=ctx, initializer=_pool_init,
+                             initargs=(barrier,)) as ex:
+        res = list(ex.map(_oracle_task, tasks))
+    units = sum(u for u, _, _ in res)
+    wall = max(t1 for _, _, t1 in res) - min(t0 for _, t0, _ in res)
+    return units / wall, k, steps, wall
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def sample_part(k, n):
     return "all of it" if k >= n else "central column"
 
@@ -320,6 +420,14 @@ def run_batched(args, dev, world):
     ms = max_over_ranks(ms_rank, world)
     st = g.stats()
     value = job_rate(b.n * args.batched_steps, ms_rank, world)
+    # whole step (graph, searches included) against HBM, with the batch's own counters at
+    # the last step; the working set (~1 GB) exceeds L2
+    peak, peak_src = measured_hbm_peak()
+    alg = algorithmic_bytes(st, st["n_active"])
+    ach = alg / (ms_rank / args.batched_steps / 1e3) / 1e9
+    roof = {"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peak, "frac": ach / peak,
+            "peak_source": peak_src, "kernel": "whole step (graph: k_begin, searches when due, step kernels)",
+            "algorithmic_bytes_per_step": alg, "bytes_per_particle_step": alg / max(st["n_active"], 1)}
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -349,12 +457,71 @@ def run_batched(args, dev, world):
     return {"workload": f"batched-drums-512 ({b.n} spheres, N log-uniform in 500-20000, r in 1-3 mm)",
             "n": b.n, "instances": len(insts), "steps": args.batched_steps, "value": value, "unit": UNIT,
             "ms_per_step": ms / args.batched_steps, "dt": b.cfg["dt"], "precision": "mixed",
-            "autotune": {"chosen": over, "candidates": table},
+            "autotune": {"chosen": over, "candidates": table}, "roofline": roof,
+            "timed_from": "the seeded fill (every step of the 10,000, including the early settling and its "
+                          "searches); the autotuner times 300 steps after 100 untimed ones",
             "rebuilds": st["rebuilds"], "n_touch_last_step": st["n_touch"],
             "plain": {"value": plain_value, "unit": UNIT, "method": "one context per drum, 16 drums timed over "
                       f"{k_steps} steps each, extrapolated to all 512 by particle count"},
             "speedup_vs_plain": value / plain_value,
             "state_vs_plain": "bit-identical per instance (tests/test_gpu_batch.py)"}
+
+
+def timed_steps(g, steps, dev, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0 = g.stats()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    s1 = g.stats()
+    ms = e0.elapsed_time(e1)
+    return ms, s0, s1
+
+
+def run_configs(args, dev, world):
+    """C1: the 1,000-sphere cube settling in FP64 (2,000 steps); C2: the 200,000-sphere
+    rotating drum in mixed precision (20,000 steps) and FP64 (2,000 steps); C3 (ii): the
+    4.3M silo discharging -- the packed bed with the orifice plug gone at t = 0, timed over
+    500 steps after 3,000 steps of developing flow (searches and removals in the window)."""
+    import torch
+    import workloads
+    from paper_2106_09576_gb300 import DEM
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    def line(g, steps, warm, extra=None):
+        g.step(warm)
+        ms, s0, s1 = timed_steps(g, steps, dev, stream)
+        act = 0.5 * (s0["n_active"] + s1["n_active"])
+        d = {"value": job_rate(act * steps, ms, world), "unit": UNIT, "steps": steps, "warmup": warm,
+             "ms_per_step": ms / steps, "searches_in_window": s1["rebuilds"] - s0["rebuilds"],
+             "n_active": s1["n_active"], "n_touch": s1["n_touch"]}
+        if extra:
+            d.update(extra)
+        g.close()
+        return d
+
+    c = workloads.cube(precision="fp64")
+    out["c1_cube_fp64"] = dict(workload=f"cube-{c.n}", precision="fp64",
+                               **line(DEM(c.cfg, c.x, c.v, c.w, c.radius, c.walls, precision="fp64", device=dev),
+                                      2000, 5))
+    for prec, steps in (("mixed", 20000), ("fp64", 2000)):
+        d = workloads.drum(precision=prec, spacing=0.999)
+        d.cfg["pair_eval"] = args.pair_eval
+        out[f"c2_drum_{prec}"] = dict(workload=f"drum-rotating-{d.n}", precision=prec,
+                                      **line(DEM(d.cfg, d.x, d.v, d.w, d.radius, d.walls, precision=prec,
+                                                 device=dev), steps, 20))
+    torch.cuda.empty_cache()
+    sl = workloads.silo(precision="mixed", spacing=0.995, jitter=0.002, t_open=0.0)
+    sl.cfg["pair_eval"] = args.pair_eval
+    out["c3_silo_discharge_mixed"] = dict(
+        workload=f"silo-discharge-{sl.n}", precision="mixed",
+        **line(DEM(sl.cfg, sl.x, sl.v, sl.w, sl.radius, sl.walls, precision="mixed", device=dev), 500, 3000))
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_ours(args):
@@ -368,8 +535,15 @@ def run_ours(args):
     if args.skin is not None:
         wl.cfg["skin"] = args.skin * 2.0 * float(wl.radius.max())
         desc += f"-skin{args.skin:g}d"
+    wl.cfg["pair_eval"] = args.pair_eval
+    once = args.pair_eval == "once"
     n = wl.n
     extra = {}
+
+    # ---------------- issue rates of the arithmetic pipes (the FP64 path's ceiling)
+    from paper_2106_09576_gb300.dem import pipe_rates
+    pipe = pipe_rates(dev)
+    extra["pipe_rates"] = {"unit": "thread instr/s", **pipe, "dfma_over_ffma": pipe["dfma"] / pipe["ffma"]}
 
     # ---------------- mixed precision, device-resident inputs, graph path
     g = DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="mixed", device=dev)
@@ -395,9 +569,12 @@ def run_ours(args):
     value = job_rate(active * args.steps, ms, world)
     rebuilds = st1["rebuilds"] - st0["rebuilds"]
     inner_builds = st1["inner_builds"] - st0["inner_builds"]
-    # k_set_remaining and k_end per dem_step call, k_begin and the step kernel per step, and
-    # the list builds (a contact search also refreshes the inner list)
-    launches = 2 + 2 * args.steps + (REBUILD_KERNELS + 1) * rebuilds + max(inner_builds - rebuilds, 0)
+    # k_set_remaining and k_end per dem_step call, k_begin and the step kernels per step
+    # (k_pair_mixed + k_int_mixed, or k_step_mixed), and the list builds (a contact search
+    # also refreshes the inner list; with one evaluation per pair a refresh is two kernels)
+    per_inner = 2 if once else 1
+    launches = (2 + (3 if once else 2) * args.steps + (REBUILD_KERNELS + per_inner) * rebuilds
+                + per_inner * max(inner_builds - rebuilds, 0))
 
     # ---------------- step-kernel roofline (CUDA events around each launch)
     kp = args.profile_steps if args.profile_steps is not None else min(args.steps, 200)
@@ -408,9 +585,10 @@ def run_ours(args):
     alg = algorithmic_bytes(st2, st2["n_active"])
     peak, peak_src = measured_hbm_peak()
     achieved = alg / (kernel_ms / 1e3) / 1e9
-    traffic = recorded_traffic(desc, st2["n_active"])
+    kname = "k_pair_mixed+k_int_mixed" if once else "k_step_mixed"
+    traffic = recorded_traffic(kname, desc, st2["n_active"])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_step_mixed", "peak_source": peak_src,
+                "traffic": traffic, "kernel": kname, "peak_source": peak_src,
                 "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": alg,
                 "bytes_per_particle_step": alg / max(st2["n_active"], 1),
                 "search_ms_avg": prof["search_ms"] / max(prof["searches"], 1), "searches": prof["searches"],
@@ -473,9 +651,26 @@ def run_ours(args):
         fv = sum_over_ranks(0.5 * (s0["n_active"] + s1["n_active"]) * kf, world) / (fms / 1e3)
         extra["fp64"] = {"value": fv, "unit": UNIT, "steps": kf, "ms_per_step": fms / kf,
                          "mixed_speedup": value / fv}
+        # the FP64 step kernel against the measured FP64 FMA rate: its FP64-pipe warp
+        # instructions per launch (ncu count per particle, committed) over its CUDA-event time
+        pf = gf.step_profiled(5)
+        fk_ms = pf["step_kernel_ms"] / max(pf["step_launches"], 1)
+        pc = recorded_pipe_counts("k_step_fp64", desc, FP64_STEP_SOURCES)
+        peak_w = pipe["dfma"] / 32.0
+        ach = None if pc is None else pc["fp64_warp_inst_per_particle"] * s1["n_active"] / (fk_ms / 1e3)
+        extra["fp64"]["roofline"] = {
+            "bound": "alu", "kernel": "k_step_fp64", "unit": "G FP64-pipe warp instr/s",
+            "achieved": None if ach is None else ach / 1e9, "peak": peak_w / 1e9,
+            "frac": None if ach is None else ach / peak_w, "kernel_ms": fk_ms,
+            "peak_source": "measured (dem_pipe_rates: FP64 FMA thread rate / 32)",
+            "fp64_warp_inst_per_particle": None if pc is None else pc["fp64_warp_inst_per_particle"]}
         gf.close()
         del gf
         torch.cuda.empty_cache()
+
+    # ---------------- the other configurations, one line each
+    if not args.no_configs:
+        extra["configs"] = run_configs(args, dev, world)
 
     # ---------------- batch of 512 independent drums in one context (one launch per step)
     if not args.no_batched:
@@ -485,16 +680,26 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu and world == 1 and rank == 0:
         rate, k, steps, dt = oracle_rate(wl, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{k} spheres of the {desc} workload ({sample_part(k, wl.n)}), {steps} steps, "
-                         f"{dt:.1f} s, single thread, host CPU of the GPU box"}
+        single = {"value": rate, "unit": UNIT, "cores": 1,
+                  "sample": f"{k} spheres of the {desc} workload ({sample_part(k, wl.n)}), {steps} steps, "
+                            f"{dt:.1f} s"}
+        cores = host_cores()
+        if cores > 1:
+            arate, ak, asteps, adt = oracle_rate_all_cores(wl, args.cpu_seconds, cores)
+            cpu = {"value": arate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{cores} single-thread oracle processes at once, each on its own ball of {ak} "
+                             f"spheres of the {desc} workload, {asteps} steps, {adt:.1f} s wall, host CPU of the "
+                             f"GPU box", "single_thread": single}
+        else:
+            cpu = dict(single, kind="oracle")
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{desc}-{n}", "n": n, "precision": "mixed", "dt": wl.cfg["dt"],
+            "config": {"workload": f"{desc}-{n}", "n": n, "precision": "mixed", "pair_eval": args.pair_eval,
+                       "dt": wl.cfg["dt"],
                        "d": float(2 * wl.radius.max()), "skin": wl.cfg.get("skin", 0.0),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (state + lists + overlaps > 129 MB)"},

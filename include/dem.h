@@ -55,6 +55,9 @@ typedef int32_t dem_status;
 #define DEM_PRECISION_MIXED 1  /* contact-force arithmetic in FP32; positions, velocities,
                                   integration and tangential-overlap accumulation in FP64 */
 
+#define DEM_PAIR_EVAL_ONCE 0   /* dem_config.pair_eval */
+#define DEM_PAIR_EVAL_BOTH 1
+
 #define DEM_MAX_WALLS 8
 #define DEM_MAX_NEIGHBORS 56   /* fine-search entries kept per particle */
 #define DEM_MAX_CONTACTS 32    /* simultaneous contacts (particles + walls) per particle */
@@ -94,7 +97,12 @@ typedef struct {
                                 (Eqs. linearkn, linearetan; same constants tangentially) */
   int32_t integrator;        /* 0 velocity Verlet (Eqs. halfstep, newvv), 1 explicit Euler
                                 (Eq. integ_EE) */
-  int32_t reserved1;
+  int32_t pair_eval;         /* mixed precision: DEM_PAIR_EVAL_ONCE (0, default) evaluates each
+                                touching pair once, by its partner of smaller id, and hands the
+                                reaction to the other (Sec. 2.1: the pair force and its
+                                reaction, Eq. torque_t); DEM_PAIR_EVAL_BOTH evaluates it from
+                                both sides.  Same pairs and law, sums in another order: a
+                                launch choice, not physics.  FP64 contexts always use BOTH */
   double linear_velocity;    /* characteristic impact velocity V of Eq. linearkn (m/s, > 0 for
                                 the linear model) */
 } dem_config;
@@ -262,6 +270,14 @@ dem_status dem_get_stats(dem_ctx* ctx, dem_stats* out);
 dem_status dem_find_pairs_static(const double* x, const uint8_t* active, int64_t n, double cutoff,
                                  const double* domain_lo, const double* domain_hi, int32_t* pairs,
                                  int64_t capacity, int64_t* count, void* stream);
+/* Measurement aid (no counterpart in the paper): issue rates of the arithmetic pipes the
+ * step kernels depend on, on the current device, in thread-level instructions per second:
+ * rates[0] FP64 fused multiply-add, rates[1] FP64 add, rates[2] FP32 fused multiply-add,
+ * rates[3] FP32 -> FP64 conversion (host array of 4).  Each from a kernel of independent
+ * chains over 8 blocks of 256 threads per SM, timed with CUDA events on `stream` after a
+ * warm-up launch; allocates nothing; synchronises.  The FP64 path's roofline is its FP64
+ * instruction rate against rates[0]. */
+dem_status dem_pipe_rates(double* rates, void* stream);
 const char* dem_status_string(dem_status s);
 void dem_destroy(dem_ctx* ctx);
 

@@ -26,6 +26,7 @@ SOURCES = {
     # additions, multiplications and FMAs stay IEEE (the double-float arithmetic needs them)
     "dem_step_mixed.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"],
     "dem_static_pairs.cu": [],
+    "dem_probe.cu": [],
     "surrogate.cu": [],
     "surrogate_tc.cu": [],
 }

@@ -84,6 +84,7 @@ dem_status derive(const dem_config* c, Derived* d) {
   if (c->contact_model == 1 && !(c->linear_velocity > 0.0 && std::isfinite(c->linear_velocity))) return DEM_ERR_ARG;
   if (c->n_instances < 0 || c->n_instances > c->n) return DEM_ERR_ARG;
   if (c->step_block != 0 && c->step_block != 32 && c->step_block != 64 && c->step_block != 128) return DEM_ERR_ARG;
+  if (c->pair_eval != DEM_PAIR_EVAL_ONCE && c->pair_eval != DEM_PAIR_EVAL_BOTH) return DEM_ERR_ARG;
   if (!valid_material(c->particle) || !valid_material(c->wall)) return DEM_ERR_ARG;
   if (!finite3(c->gravity) || !finite3(c->domain_lo) || !finite3(c->domain_hi)) return DEM_ERR_ARG;
   // search threshold: r_c = d_max + skin, or factor * d_max (Sec. 3.2), same arithmetic
@@ -126,7 +127,8 @@ dem_status derive(const dem_config* c, Derived* d) {
 
 struct Offsets {
   size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], inst[2], itab, xref, nbr, nbr_cnt,
-      inner, inner_j, inner_cnt, xin, key, local, order,
+      nbr_lo, inner_lo, inner_m, rec, upart,
+      inner, inner_j, inner_cnt, xin, key, local, members, order,
       cell_count, cell_start, scan_tmp, hkey, hval, wall_tmp, wall_tmp_mask, out_v, out_w, out_F, out_M,
       stage, ctl, io_cnt, io_off;
   size_t total;
@@ -156,15 +158,23 @@ Offsets layout(const dem_config* c, const Derived& d) {
   o.xref = L.add(3 * n * 8);
   o.nbr = L.add(n * kMaxNbr * 4);
   o.nbr_cnt = L.add(n * 4);
+  o.nbr_lo = L.add(n);
   {
     const bool mixed = c->precision == DEM_PRECISION_MIXED;   // the inner list of the mixed path
     o.inner = L.add(mixed ? n * kInnerMax : 0);
     o.inner_j = L.add(mixed ? n * kInnerMax * 4 : 0);
     o.inner_cnt = L.add(mixed ? n : 0);
     o.xin = L.add(mixed ? 7 * n * 4 : 0);
+    // one evaluation per pair: partner positions, pushed reactions, owners' own sums
+    const bool once = mixed && c->pair_eval == DEM_PAIR_EVAL_ONCE;
+    o.inner_lo = L.add(once ? n : 0);
+    o.inner_m = L.add(once ? n * kInnerMax : 0);
+    o.rec = L.add(once ? n * kInnerMax * 32 : 0);
+    o.upart = L.add(once ? n * 32 : 0);
   }
   o.key = L.add(n * 4);
   o.local = L.add(n * 4);
+  o.members = L.add(n * 4);
   o.order = L.add(n * 4);
   o.cell_count = L.add(((size_t)d.n_cells + 1) * 4);
   o.cell_start = L.add(((size_t)d.n_cells + 2) * 4);
@@ -836,12 +846,19 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   P.xref = (double*)(base + o.xref);
   P.nbr = (int*)(base + o.nbr);
   P.nbr_cnt = (int*)(base + o.nbr_cnt);
+  P.nbr_lo = (uint8_t*)(base + o.nbr_lo);
+  P.pair_once = (cfg->precision == DEM_PRECISION_MIXED && cfg->pair_eval == DEM_PAIR_EVAL_ONCE) ? 1 : 0;
+  P.inner_lo = (uint8_t*)(base + o.inner_lo);
+  P.inner_m = (uint8_t*)(base + o.inner_m);
+  P.rec = (float4*)(base + o.rec);
+  P.upart = (float4*)(base + o.upart);
   P.inner = (uint8_t*)(base + o.inner);
   P.inner_j = (int*)(base + o.inner_j);
   P.inner_cnt = (uint8_t*)(base + o.inner_cnt);
   P.xin = (float*)(base + o.xin);
   P.key = (unsigned*)(base + o.key);
   P.local = (int*)(base + o.local);
+  P.members = (int*)(base + o.members);
   P.order = (int*)(base + o.order);
   P.cell_count = (int*)(base + o.cell_count);
   P.cell_start = (int*)(base + o.cell_start);

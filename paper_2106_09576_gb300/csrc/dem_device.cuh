@@ -25,6 +25,11 @@
 //                                     list whose partner was within R_i + R_j + delta at the
 //                                     last inner build, ascending (so in partner-id order)
 //     inner_j           int32 [n][32] (mixed path) the partners of those slots
+//     inner_lo, inner_m uint8 [n], [n][32] (mixed path, one evaluation per pair): the
+//                                     leading slots whose partner has the smaller id, and
+//                                     for the other slots the own position in the partner's row
+//     rec, upart        float4 [32][n][2], [2][n] (same): reactions pushed by owners to
+//                                     their partners, and each owner's own partial sums
 //     xin               FP32 [7][n]   (mixed path) positions at the last inner build, hi
 //                                     parts then lo parts, then the distance of that position
 //                                     from the search reference x_ref (rounded up)
@@ -144,6 +149,7 @@ struct Params {
   int contact_model;    // 0 non-linear, 1 linear (Eqs. linearkn, linearetan)
   int integrator;       // 0 velocity Verlet, 1 explicit Euler (Eq. integ_EE)
   int any_translating;  // some wall (of the context or of an instance) translates
+  int pair_once;        // mixed path: each pair evaluated once by its owner (see below)
   double lin_V;         // characteristic impact velocity of Eq. linearkn
   float f_lin_V;
   int rebuild_every;
@@ -189,12 +195,24 @@ struct Params {
   float4* render[2];    // [n][3] FP32 {x_lo, flag} {v, w_x} {w_y, w_z, 0, 0}
   int* nbr;
   int* nbr_cnt;
+  uint8_t* nbr_lo;      // [n] entries of the fine-search list with a smaller partner id
   uint8_t* inner;       // [n][kInnerMax] (mixed path)
   int* inner_j;         // [n][kInnerMax] partner of each inner slot
   uint8_t* inner_cnt;   // [n]
+  // one evaluation per pair (mixed path, pair_once): the pair belongs to its partner of
+  // smaller id (the owner).  inner_lo: leading slots of a particle's inner list whose
+  // partners own the pair; inner_m: for an owned slot, where the owner sits in the
+  // partner's inner list; rec: slot-major [kInnerMax][n][2] the reaction an owner
+  // computed for its partner {F, M_x}{M_y, M_z, 0, 0}; upart [2][n]: the owner's own sum
+  // of its owned pairs and walls, same packing
+  uint8_t* inner_lo;    // [n]
+  uint8_t* inner_m;     // [n][kInnerMax]
+  float4* rec;
+  float4* upart;
   float* xin;           // [7][n]
   unsigned* key;        // [n] cell key of the current (pre-sort) order
-  int* local;           // [n] slot within the cell
+  int* local;           // [n] slot within the cell (order of the atomics)
+  int* members;         // [n] particles grouped by cell, any order within a cell
   int* order;           // [n] sorted position -> previous position
   int* cell_count;      // [n_cells + 1]
   int* cell_start;      // [n_cells + 2]
@@ -362,6 +380,7 @@ void launch_hist_clear(const Params& P, cudaStream_t s, int force);
 void scan_exclusive_i32(const int* in, int n, int* out, int* partials, cudaStream_t s);
 void launch_step_fp64(const Params& P, cudaStream_t s);
 void launch_step_mixed(const Params& P, cudaStream_t s);
+void launch_inner_mirror(const Params& P, cudaStream_t s);
 
 constexpr int kStepBlock = 128;   // largest block of the step kernels
 

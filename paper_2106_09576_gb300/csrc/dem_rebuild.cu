@@ -169,24 +169,28 @@ __global__ void k_cell_count(Params P) {
 __global__ void k_cell_scatter(Params P) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.n) return;
-  P.order[P.cell_start[P.key[p]] + P.local[p]] = p;
+  P.members[P.cell_start[P.key[p]] + P.local[p]] = p;
 }
 
 // Orders each cell's members by previous position: the sort becomes stable and
-// independent of the order in which the atomics were served.
+// independent of the order in which the atomics were served.  One thread per member: it
+// counts the members of its cell with a smaller previous position and lands there, so a
+// crowded cell costs each of its m members O(m) work (as the fine search over it does)
+// and no thread sorts a whole cell.  The bucket of particles that left the system keeps
+// any order.
 __global__ void k_cell_order(Params P) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= P.n_cells) return;  // the out-of-system bucket keeps any order
-  const int b = P.cell_start[c], e = P.cell_start[c + 1];
-  for (int a = b + 1; a < e; a++) {
-    int v = P.order[a];
-    int k = a - 1;
-    while (k >= b && P.order[k] > v) {
-      P.order[k + 1] = P.order[k];
-      k--;
-    }
-    P.order[k + 1] = v;
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= P.n) return;
+  const int p = P.members[s];
+  const int c = P.key[p];
+  if (c >= P.n_cells) {
+    P.order[s] = p;
+    return;
   }
+  const int b = P.cell_start[c], e = P.cell_start[c + 1];
+  int r = 0;
+  for (int t = b; t < e; t++) r += P.members[t] < p ? 1 : 0;
+  P.order[b + r] = p;
 }
 
 // ------------------------------------------------------------------ 3. permute
@@ -328,8 +332,13 @@ __global__ void __launch_bounds__(kNbrBlock) k_neighbors(Params P) {
       }
     }
   }
-  for (int k = 0; k < cnt; k++) out[k] = ri[k];
+  int nlo = 0;   // the list is ordered by partner id: its partners of smaller id lead
+  for (int k = 0; k < cnt; k++) {
+    out[k] = ri[k];
+    nlo += rd[k] < ids[q] ? 1 : 0;
+  }
   P.nbr_cnt[q] = cnt;
+  P.nbr_lo[q] = (uint8_t)nlo;
   if (overflow) atomicOr(&P.ctl->status, kStCapacity);
   // one atomic per warp for the search statistics (not two per particle on two words)
   const unsigned act = __activemask();
@@ -375,6 +384,7 @@ __global__ void k_hist_load(Params P) {
     const float up = reach + hi_distance_error(ai, max_abs3(hj), 2.0f * reach);
     if (ex * ex + ey * ey + ez * ez > up * up * (1.0f + 1e-6f)) continue;
     const int b = ids[j];
+    if (P.pair_once && b < a) continue;   // one evaluation per pair: the owner keeps the overlap
     const unsigned long long key = pair_key(a, b);
     unsigned h = hash_slot(key, P.hcap_mask);
     for (unsigned probe = 0; probe <= P.hcap_mask; probe++) {
@@ -440,7 +450,8 @@ __global__ void k_inner_build(Params P) {
   const int cnt = P.nbr_cnt[q];
   uint8_t* row = P.inner + (size_t)q * kInnerMax;
   int* rowj = P.inner_j + (size_t)q * kInnerMax;
-  int m = 0;
+  int m = 0, mlo = 0;
+  const int nlo = P.nbr_lo[q];
   bool overflow = false;
   for (int k = 0; k < cnt; k++) {
     const int j = nb[k];
@@ -453,11 +464,13 @@ __global__ void k_inner_build(Params P) {
       row[m] = (uint8_t)k;
       rowj[m] = j;
       m++;
+      mlo += k < nlo ? 1 : 0;
     } else {
       overflow = true;
     }
   }
   P.inner_cnt[q] = (uint8_t)m;
+  if (P.pair_once) P.inner_lo[q] = (uint8_t)mlo;
   if (overflow) atomicOr(&C->status, kStCapacity);
   const float* xr = reinterpret_cast<const float*>(P.xref);
   const float h[3] = {hi.x, hi.y, hi.z}, l[3] = {lo4.x, lo4.y, lo4.z};
@@ -473,10 +486,40 @@ __global__ void k_inner_build(Params P) {
   P.xin[6 * n + q] = sqrtf(d2) * (1.0f + 1e-5f);
 }
 
+// One evaluation per pair: for every slot of a particle's inner list whose pair it owns
+// (partner of larger id), the position of the particle in the partner's inner list, where
+// the step pushes the reaction.  The inner test is symmetric (the same FP32 operations on
+// both sides), so the partner's row holds the owner among its leading, foreign-owned
+// slots; a row truncated at kInnerMax has already raised the capacity error, and a slot
+// whose owner is not found is marked 255 and never written.
+__global__ void k_inner_mirror(Params P) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= P.ctl->n_act_sorted) return;
+  const int cnt = P.inner_cnt[q], lo = P.inner_lo[q];
+  const int* rowj = P.inner_j + (size_t)q * kInnerMax;
+  uint8_t* mrow = P.inner_m + (size_t)q * kInnerMax;
+  bool missing = false;
+  for (int s = lo; s < cnt; s++) {
+    const int j = rowj[s];
+    const int* pj = P.inner_j + (size_t)j * kInnerMax;
+    const int jlo = P.inner_lo[j];
+    int m = 255;
+    for (int t = 0; t < jlo; t++)
+      if (pj[t] == q) {
+        m = t;
+        break;
+      }
+    missing |= m == 255;
+    mrow[s] = (uint8_t)m;
+  }
+  if (missing) atomicOr(&P.ctl->status, kStCapacity);
+}
+
 void launch_inner(const Params& P, cudaStream_t s) {
   if (P.precision != DEM_PRECISION_MIXED) return;
   const int T = 256;
   k_inner_build<<<(P.n + T - 1) / T, T, 0, s>>>(P);
+  if (P.pair_once) k_inner_mirror<<<(P.n + T - 1) / T, T, 0, s>>>(P);
 }
 
 __global__ void k_rebuild_begin(Params P) {
@@ -526,7 +569,7 @@ void launch_rebuild(const Params& P, cudaStream_t s) {
   k_cell_count<<<nb, T, 0, s>>>(P);
   scan_exclusive_i32(P.cell_count, P.n_cells + 1, P.cell_start, P.scan_tmp, s);
   k_cell_scatter<<<nb, T, 0, s>>>(P);
-  k_cell_order<<<(P.n_cells + 1 + T - 1) / T, T, 0, s>>>(P);
+  k_cell_order<<<nb, T, 0, s>>>(P);
   // 3. permutation
   k_permute<<<nb, T, 0, s>>>(P);
   k_mirror_inactive<<<nb, T, 0, s>>>(P);

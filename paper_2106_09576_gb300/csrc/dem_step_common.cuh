@@ -188,11 +188,14 @@ __device__ __forceinline__ bool wall_maybe_f(int kind, const WallF& W, const flo
 // ------------------------------------------------------------------ FP32 contact law
 // kExt: the paper's other options (linear model, viscous rolling) may occur; without it
 // they are compiled out, and the kernel keeps the registers of the default model.
+// Outputs the pieces of one contact: Fp = F_n + F_t on the particle, n x F_t (times the
+// lever R_i on the particle, R_j on its partner) and the rolling torque M_r (on the
+// partner: -M_r, Table rolling_torque's w_ji = -w_ij).
 template <bool kExt>
-__device__ __forceinline__ void law_f(const float* nrm, float dn, const float* vij, const float* dw,
-                                      const float* vom, float Re, float me, float Ye, float Ge, float ceta,
-                                      float mu, float mur, int rolling, const float* lin, float dt, double* H,
-                                      bool incr, float Ri, float* F, float* M) {
+__device__ __forceinline__ void law_pieces_f(const float* nrm, float dn, const float* vij, const float* dw,
+                                             const float* vom, float Re, float me, float Ye, float Ge, float ceta,
+                                             float mu, float mur, int rolling, const float* lin, float dt, double* H,
+                                             bool incr, float* Fp, float* nxFt, float* Mr) {
   float vn = vij[0] * nrm[0] + vij[1] * nrm[1] + vij[2] * nrm[2];
   float vrn[3], vrt[3];
   for (int d = 0; d < 3; d++) {
@@ -233,9 +236,10 @@ __device__ __forceinline__ void law_f(const float* nrm, float dn, const float* v
       H[d] = f2d_int((Ft[d] + eta_t * vrt[d]) * ikt);
     }
   }
-  float nxFt[3] = {nrm[1] * Ft[2] - nrm[2] * Ft[1], nrm[2] * Ft[0] - nrm[0] * Ft[2],
-                   nrm[0] * Ft[1] - nrm[1] * Ft[0]};
-  float Mr[3] = {0.f, 0.f, 0.f};
+  nxFt[0] = nrm[1] * Ft[2] - nrm[2] * Ft[1];
+  nxFt[1] = nrm[2] * Ft[0] - nrm[0] * Ft[2];
+  nxFt[2] = nrm[0] * Ft[1] - nrm[1] * Ft[0];
+  Mr[0] = Mr[1] = Mr[2] = 0.f;
   if (rolling == 1 && (dw[0] != 0.f || dw[1] != 0.f || dw[2] != 0.f)) {
     // unit vector of w_i - w_j, scaled first so that tiny relative spins do not underflow
     const float s = 1.0f / fmaxf(fmaxf(fabsf(dw[0]), fabsf(dw[1])), fabsf(dw[2]));
@@ -250,8 +254,19 @@ __device__ __forceinline__ void law_f(const float* nrm, float dn, const float* v
     const float c = -mur * Re * aFn * avw * rsqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     for (int d = 0; d < 3; d++) Mr[d] = c * u[d];
   }
+  for (int d = 0; d < 3; d++) Fp[d] = Fn[d] + Ft[d];
+}
+
+// One contact added to the particle's sums: F += F_n + F_t, M += R_i n x F_t + M_r.
+template <bool kExt>
+__device__ __forceinline__ void law_f(const float* nrm, float dn, const float* vij, const float* dw,
+                                      const float* vom, float Re, float me, float Ye, float Ge, float ceta,
+                                      float mu, float mur, int rolling, const float* lin, float dt, double* H,
+                                      bool incr, float Ri, float* F, float* M) {
+  float Fp[3], nxFt[3], Mr[3];
+  law_pieces_f<kExt>(nrm, dn, vij, dw, vom, Re, me, Ye, Ge, ceta, mu, mur, rolling, lin, dt, H, incr, Fp, nxFt, Mr);
   for (int d = 0; d < 3; d++) {
-    F[d] += Fn[d] + Ft[d];
+    F[d] += Fp[d];
     M[d] += Ri * nxFt[d] + Mr[d];
   }
 }
@@ -301,13 +316,13 @@ __device__ __forceinline__ void block_flush(const StepStats& s, Control* C) {
 // one atomic per failing thread).  The parities of the state and the history flip after
 // the kernel: it only marks the flip as due (a plain store of one thread), and the next
 // k_begin or the k_end closing the call applies it (apply_flip), so no block waits on a
-// grid-wide count.
-__device__ __forceinline__ void end_step(const StepStats& st, Control* C, bool last) {
+// grid-wide count.  A step made of two kernels marks it from the second only.
+__device__ __forceinline__ void end_step(const StepStats& st, Control* C, bool last, bool closes_step = true) {
   if (last)
     block_flush(st, C);
   else if (st.status)
     atomicOr(&C->status, st.status);
-  if (blockIdx.x == 0 && threadIdx.x == 0) C->flip_due = 1;
+  if (closes_step && blockIdx.x == 0 && threadIdx.x == 0) C->flip_due = 1;
 }
 
 // Exact "z < z_sink" on FP64 values with integer operations.

@@ -355,12 +355,364 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
   end_step(st, P.ctl, last);
 }
 
+// ====================================================================== one evaluation per pair
+// A touching pair is evaluated once, by its partner of smaller id (the owner), with the
+// law and operations of the kernel above: the two sides of a pair compute exact opposites
+// there (Sec. 2.1: the pair force and its reaction; Eq. torque_t, with the same n x F_t on
+// both sides; Table rolling_torque, w_ji = -w_ij), so the owner's numbers give the
+// partner's contribution exactly.  The step is two kernels:
+//   k_pair_mixed  per owner: its owned inner slots (partners of larger id, in id order)
+//                 and its walls; the owner's own sum into upart, the partner's reaction
+//                 -F, R_j n x F_t - M_r into the partner's record rec[m][j] (m: the
+//                 owner's slot in the partner's inner list), zeros for a pair that does
+//                 not touch; the owner keeps the pair's tangential overlap;
+//   k_int_mixed   per particle: the records of its leading slots (partners that own the
+//                 pair, in id order), plus its own sum, then integration as above.
+// Every sum has a fixed order given by the touching pairs alone (records first, then the
+// owner's pairs in id order, then walls), so a trajectory does not depend on when the
+// lists are rebuilt; no float atomics.
+__device__ __forceinline__ void put_rec(const Params& P, int m, int j, const float* f, const float* t) {
+  float4* r = P.rec + 2 * ((size_t)m * P.n + j);
+  r[0] = make_float4(f[0], f[1], f[2], t[0]);
+  r[1] = make_float4(t[1], t[2], 0.0f, 0.0f);
+}
+
+template <bool kBatch, bool kExt>
+__global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_constant__ Params P) {
+  const Control* C = P.ctl;
+  const int cur = C->cur, hc = C->hc;
+  const bool init = C->init != 0, last = C->last != 0;
+  const unsigned wall_on = C->wall_on;
+  const int n = P.n, nact = C->n_act_sorted;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  StepStats st = {0u, 0u, 0u, 0.0f, 0u};
+  const double* X = P.x[cur];
+  const float4* SH = P.shadow[cur];
+  const float4* RD = P.render[cur];
+  if (i < nact) {
+    const int icnt = P.inner_cnt[i], ilo = P.inner_lo[i];
+    const uint8_t* irow = P.inner + (size_t)i * kInnerMax;
+    const uint8_t* mrow = P.inner_m + (size_t)i * kInnerMax;
+    const int* jrow = P.inner_j + (size_t)i * kInnerMax;
+    const float4 o0 = SH[i];
+    const float4 o1 = RD[3 * (size_t)i];
+    const float zero[3] = {0.f, 0.f, 0.f};
+    float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
+    if (o1.w == 0.0f) {
+      // out of the system: its pairs exert nothing, and its partners' records say so
+      for (int s = ilo; s < icnt; s++) {
+        const int m = mrow[s];
+        if (m != 255) put_rec(P, m, jrow[s], zero, zero);
+      }
+      P.mask[hc ^ 1][i] = 0ull;
+    } else {
+      const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o1.x, o1.y, o1.z};
+      const float Rif = o0.w;
+      const InstDev* I = kBatch ? P.itab + P.inst[C->sbuf][i] : nullptr;
+      const MatF& Mt = kBatch ? I->mf : P.mf;
+      const float4 o2 = RD[3 * (size_t)i + 1], o3 = RD[3 * (size_t)i + 2];
+      const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
+      const unsigned long long mold = P.mask[hc][i];
+      const double* Hold = P.hist[hc] + (size_t)i * kHistStride * 3;
+      double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHistStride * 3;
+      const float mif = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rif * Rif * Rif;
+      const float dtf = P.f_dt;
+      unsigned long long mnew = 0ull;
+      int rank = 0;
+      for (int s = ilo; s < icnt; s++) {
+        const int k = irow[s];
+        const int j = jrow[s];
+        const int m = mrow[s];
+        const float4 r0 = SH[j];
+        const float4* rj = RD + 3 * (size_t)j;
+        const float4 r1 = rj[0], r2 = rj[1], r3 = rj[2];
+        double H[3] = {0.0, 0.0, 0.0};
+        if ((mold >> k) & 1ull) {
+          const int ro = __popcll(mold & ((1ull << k) - 1ull));
+          H[0] = Hold[ro * 3];
+          H[1] = Hold[ro * 3 + 1];
+          H[2] = Hold[ro * 3 + 2];
+        }
+        float rf[3] = {0.f, 0.f, 0.f}, rm[3] = {0.f, 0.f, 0.f};
+        bool touch = false;
+        float Rjf = 0.f, D = 0.f, Sh = 0.f, Ah = 0.f, Al = 0.f;
+        float s3[3], t3[3];
+        if (r1.w != 0.0f) {                              // partner in the system
+          Rjf = r0.w;
+          df_diff(hx[0], lx[0], r0.x, r1.x, s3[0], t3[0]);
+          df_diff(hx[1], lx[1], r0.y, r1.y, s3[1], t3[1]);
+          df_diff(hx[2], lx[2], r0.z, r1.z, s3[2], t3[2]);
+          // S^2 - r^2 as an exact double-float
+          float p2, pe, e;
+          two_prod(s3[0], s3[0], Ah, pe);
+          Al = pe + (2.0f * s3[0] + t3[0]) * t3[0];
+          two_prod(s3[1], s3[1], p2, pe);
+          two_sum(Ah, p2, Ah, e);
+          Al += e + pe + (2.0f * s3[1] + t3[1]) * t3[1];
+          two_prod(s3[2], s3[2], p2, pe);
+          two_sum(Ah, p2, Ah, e);
+          Al += e + pe + (2.0f * s3[2] + t3[2]) * t3[2];
+          float Sl, P2, P2e, Dh, De;
+          two_sum(Rif, Rjf, Sh, Sl);
+          two_prod(Sh, Sh, P2, P2e);
+          P2e += 2.0f * Sh * Sl;
+          two_sum(P2, -Ah, Dh, De);
+          D = Dh + (De + (P2e - Al));
+          touch = D > 0.0f;
+        }
+        if (touch) {
+          float dxf[3];
+          for (int d = 0; d < 3; d++) dxf[d] = s3[d] + t3[d];
+          const float S = Rif + Rjf;
+          const float r = sqrtf(Ah + Al);
+          const float dn = D / (Sh + r);                   // Eq. deltan without cancellation
+          const float ir = 1.0f / r;
+          const float nrm[3] = {dxf[0] * ir, dxf[1] * ir, dxf[2] * ir};   // Eq. vecn
+          const float wj[3] = {r2.w, r3.x, r3.y};
+          const float dv[3] = {vif[0] - r2.x, vif[1] - r2.y, vif[2] - r2.z};
+          const float dw[3] = {wif[0] - wj[0], wif[1] - wj[1], wif[2] - wj[2]};
+          float rw[3];
+          for (int d = 0; d < 3; d++) rw[d] = __fadd_rn(__fmul_rn(Rif, wif[d]), __fmul_rn(Rjf, wj[d]));
+          const float rwxn[3] = {rw[1] * nrm[2] - rw[2] * nrm[1], rw[2] * nrm[0] - rw[0] * nrm[2],
+                                 rw[0] * nrm[1] - rw[1] * nrm[0]};
+          const float vij[3] = {dv[0] + rwxn[0], dv[1] + rwxn[1], dv[2] + rwxn[2]};
+          const float Re = Rif * Rjf / S;
+          const float mj = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rjf * Rjf * Rjf;
+          const float me = mif * mj / (mif + mj);
+          const float lin[2] = {P.f_lin_V, Mt.lin_den_pp};
+          float Fp[3], nxFt[3], Mr[3];
+          law_pieces_f<kExt>(nrm, dn, vij, dw, rwxn, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp,
+                             P.rolling, P.contact_model == 1 ? lin : nullptr, dtf, H, !init, Fp, nxFt, Mr);
+          for (int d = 0; d < 3; d++) {
+            Ff[d] += Fp[d];
+            Mf[d] += Rif * nxFt[d] + Mr[d];
+            rf[d] = -Fp[d];
+            rm[d] = Rjf * nxFt[d] - Mr[d];
+          }
+          st.touch += 2u;
+          st.max_ovl = fmaxf(st.max_ovl, dn / fminf(Rif, Rjf));
+          if (rank < kHistStride) {
+            Hnew[rank * 3] = H[0];
+            Hnew[rank * 3 + 1] = H[1];
+            Hnew[rank * 3 + 2] = H[2];
+            mnew |= 1ull << k;
+            rank++;
+          } else {
+            st.status |= kStCapacity;
+          }
+        }
+        if (m != 255) put_rec(P, m, j, rf, rm);
+      }
+
+      // ---------------- particle-wall contacts (FP32 prefilter, then out of line)
+      const float xf[3] = {hx[0] + lx[0], hx[1] + lx[1], hx[2] + lx[2]};
+      const WallDev* WLs = kBatch ? I->walls : P.walls;
+      const WallF* WFs = kBatch ? I->wf : P.wf;
+      const int n_walls = kBatch ? I->n_walls : P.n_walls;
+      unsigned won = wall_on;
+      if (kBatch) {
+        won = 0u;
+        const double t = (double)C->step * P.dt;
+        for (int k = 0; k < n_walls; k++)
+          if (t >= WLs[k].t_on && t < WLs[k].t_off) won |= 1u << k;
+      }
+      const float t_now = (float)C->step * P.f_dt;
+      for (int k = 0; k < n_walls; k++) {
+        if (!((won >> k) & 1u)) continue;
+        if (kExt) {
+          const float* wv = kBatch ? I->wf_v[k] : P.wf_v[k];
+          const float xs[3] = {xf[0] - wv[0] * t_now, xf[1] - wv[1] * t_now, xf[2] - wv[2] * t_now};
+          if (!wall_maybe_f(WLs[k].kind, WFs[k], xs, Rif, P.wall_margin)) continue;
+        } else if (!wall_maybe_f(WLs[k].kind, WFs[k], xf, Rif, P.wall_margin)) {
+          continue;
+        }
+        const WallOut o = wall_contact_mixed<kBatch, kExt>(&P, I, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold,
+                                                     Hold, init);
+        if (!o.hit) continue;
+        for (int d = 0; d < 3; d++) {
+          Ff[d] += o.F[d];
+          Mf[d] += o.M[d];
+        }
+        st.max_ovl = fmaxf(st.max_ovl, o.ovl);
+        st.wtouch++;
+        if (rank < kHistStride) {
+          Hnew[rank * 3] = o.H[0];
+          Hnew[rank * 3 + 1] = o.H[1];
+          Hnew[rank * 3 + 2] = o.H[2];
+          mnew |= 1ull << (kMaxNbr + k);
+          rank++;
+        } else {
+          st.status |= kStCapacity;
+        }
+      }
+      P.mask[hc ^ 1][i] = mnew;
+    }
+    P.upart[i] = make_float4(Ff[0], Ff[1], Ff[2], Mf[0]);
+    P.upart[n + i] = make_float4(Mf[1], Mf[2], 0.0f, 0.0f);
+  }
+  if (P.max_overlap_ratio > 0.0 && st.max_ovl > (float)P.max_overlap_ratio) st.status |= kStOverlap;
+  end_step(st, P.ctl, last, false);
+}
+
+constexpr int kIntBlock = 256;
+
+template <bool kExt>
+__global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__ Params P) {
+  const Control* C = P.ctl;
+  const int cur = C->cur, nxt = cur ^ 1, hc = C->hc;
+  const bool init = C->init != 0, last = C->last != 0;
+  const int n = P.n, nact = C->n_act_sorted;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  StepStats st = {0u, 0u, 0u, 0.0f, 0u};
+  const double* X = P.x[cur];
+  const double* V = P.v[cur];
+  const double* W = P.w[cur];
+  const float4* SH = P.shadow[cur];
+  const float4* RD = P.render[cur];
+  float4* SHo = P.shadow[nxt];
+  float4* RDo = P.render[nxt];
+
+  if (last && i >= nact && i < n) {
+    for (int d = 0; d < 3; d++) {   // out of the system: frozen in both buffers
+      P.out_v[d * n + i] = V[d * n + i];
+      P.out_w[d * n + i] = W[d * n + i];
+      P.out_F[d * n + i] = 0.0;
+      P.out_M[d * n + i] = 0.0;
+    }
+  }
+  if (i < nact) {
+    const float4 o0 = SH[i];
+    const float4 o1 = RD[3 * (size_t)i];
+    if (o1.w == 0.0f) {
+      for (int d = 0; d < 3; d++) {
+        const double xv = X[d * n + i], vv = V[d * n + i], wv = W[d * n + i];
+        P.x[nxt][d * n + i] = xv;
+        P.v[nxt][d * n + i] = vv;
+        P.w[nxt][d * n + i] = wv;
+        if (last) {
+          P.out_v[d * n + i] = vv;
+          P.out_w[d * n + i] = wv;
+          P.out_F[d * n + i] = 0.0;
+          P.out_M[d * n + i] = 0.0;
+        }
+      }
+      P.act[nxt][i] = 0;
+      SHo[i] = o0;
+      for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
+    } else {
+      const float Rif = o0.w;
+      // reactions pushed by the owners of the leading slots, in partner-id order
+      const int ilo = P.inner_lo[i];
+      float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
+      for (int s = 0; s < ilo; s++) {
+        const float4* r = P.rec + 2 * ((size_t)s * n + i);
+        const float4 a = r[0], b = r[1];
+        Ff[0] += a.x;
+        Ff[1] += a.y;
+        Ff[2] += a.z;
+        Mf[0] += a.w;
+        Mf[1] += b.x;
+        Mf[2] += b.y;
+      }
+      const float4 u0 = P.upart[i], u1 = P.upart[n + i];
+      Ff[0] += u0.x;
+      Ff[1] += u0.y;
+      Ff[2] += u0.z;
+      Mf[0] += u0.w;
+      Mf[1] += u1.x;
+      Mf[2] += u1.y;
+
+      // ---------------- velocity Verlet in FP64 with FP32 accelerations (Eqs. main1, main2),
+      // or explicit Euler (Eq. integ_EE: x^{n+1} = x^n + v^n dt, v^{n+1} = v^n + a^n dt)
+      const float mif = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rif * Rif * Rif;
+      const float inv_m = 1.0f / mif;
+      const float inv_I = 1.0f / (0.4f * mif * Rif * Rif);
+      double xn[3], vn[3], wn[3];
+      for (int d = 0; d < 3; d++) {
+        const double xi = X[d * n + i], vi = V[d * n + i], wi = W[d * n + i];
+        const double a = f2d_int(Ff[d] * inv_m + P.f_g[d]);
+        const double al = f2d_int(Mf[d] * inv_I);
+        const bool euler = kExt && P.integrator == 1;
+        if (init && !euler) {
+          vn[d] = fma(a, P.half_dt, vi);
+          wn[d] = fma(al, P.half_dt, wi);
+        } else {
+          vn[d] = fma(a, P.dt, vi);
+          wn[d] = fma(al, P.dt, wi);
+        }
+        if (last) {
+          P.out_v[d * n + i] = (init || euler) ? vi : fma(a, P.half_dt, vi);
+          P.out_w[d * n + i] = (init || euler) ? wi : fma(al, P.half_dt, wi);
+          P.out_F[d * n + i] = f2d_int(Ff[d]);
+          P.out_M[d * n + i] = f2d_int(Mf[d]);
+        }
+        xn[d] = fma(euler ? vi : vn[d], P.dt, xi);
+        P.x[nxt][d * n + i] = xn[d];
+        P.v[nxt][d * n + i] = vn[d];
+        P.w[nxt][d * n + i] = wn[d];
+      }
+      const bool alive = !below_sink(xn[2], P.z_sink_key);
+      P.act[nxt][i] = alive ? 1 : 0;
+      float hn[3], ln[3];
+      for (int d = 0; d < 3; d++) split_df(xn[d], hn[d], ln[d]);
+      write_render(SHo + i, RDo + 3 * (size_t)i, hn, ln, vn, wn, Rif, alive);
+      if (!(finite_d(xn[0]) && finite_d(xn[1]) && finite_d(xn[2]) && finite_d(vn[0]) && finite_d(vn[1]) &&
+            finite_d(vn[2])))
+        st.status |= kStNonfinite;
+      if (alive) {
+        st.active++;
+        const float* xr = P.xin;
+        float d2 = 0.f;
+        for (int d = 0; d < 3; d++) {
+          float s1, t1;
+          df_diff(xr[d * n + i], xr[(3 + d) * n + i], hn[d], ln[d], s1, t1);
+          const float u = s1 + t1;
+          d2 += u * u;
+        }
+        if (d2 > P.f_inner_lim2) P.ctl->need_inner = 1;
+        if (P.rebuild_every <= 0 && sqrtf(d2) * (1.0f + 1e-5f) + xr[6 * n + i] > P.f_disp_lim * (1.0f - 1e-5f)) {
+          const float* xs = reinterpret_cast<const float*>(P.xref);
+          float e2 = 0.f;
+          for (int d = 0; d < 3; d++) {
+            float s1, t1;
+            df_diff(xs[d * n + i], xs[(3 + d) * n + i], hn[d], ln[d], s1, t1);
+            const float u = s1 + t1;
+            e2 += u * u;
+          }
+          if (e2 > P.f_disp_lim2) P.ctl->need_rebuild = 1;
+        }
+      }
+    }
+  }
+  (void)hc;
+  end_step(st, P.ctl, last, true);
+}
+
 void launch_step_mixed(const Params& P, cudaStream_t s) {
   const int T = P.step_block > 0 ? P.step_block : step_block(P.n, P.sm_count);
   const int blocks = (P.n + T - 1) / T;
   // the paper's other options (linear model, viscous rolling, explicit Euler, translating
   // walls) run in their own instantiation, so the default one keeps its registers
   const bool ext = P.contact_model != 0 || P.rolling == 2 || P.integrator != 0 || P.any_translating;
+  if (P.pair_once) {
+    if (P.n_inst > 1) {
+      if (ext)
+        k_pair_mixed<true, true><<<blocks, T, 0, s>>>(P);
+      else
+        k_pair_mixed<true, false><<<blocks, T, 0, s>>>(P);
+    } else {
+      if (ext)
+        k_pair_mixed<false, true><<<blocks, T, 0, s>>>(P);
+      else
+        k_pair_mixed<false, false><<<blocks, T, 0, s>>>(P);
+    }
+    const int bi = (P.n + kIntBlock - 1) / kIntBlock;
+    if (ext)
+      k_int_mixed<true><<<bi, kIntBlock, 0, s>>>(P);
+    else
+      k_int_mixed<false><<<bi, kIntBlock, 0, s>>>(P);
+    return;
+  }
   if (P.n_inst > 1) {
     if (ext)
       k_step_mixed<true, true><<<blocks, T, 0, s>>>(P);

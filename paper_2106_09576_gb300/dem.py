@@ -17,10 +17,12 @@ DEM_OK = 0
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_CAPACITY", 4: "ERR_NONFINITE",
                 5: "ERR_OVERLAP", 6: "ERR_TIMEOUT", 7: "ERR_STATE"}
 PRECISION = {"fp64": 0, "mixed": 1}
+PAIR_EVAL = {"once": 0, "both": 1}
 EXPORTED = ["dem_workspace_bytes", "dem_create", "dem_set_walls", "dem_step", "dem_step_profiled", "dem_sync",
             "dem_get_state",
             "dem_set_state", "dem_get_forces", "dem_get_pairs", "dem_get_history", "dem_set_history",
-            "dem_get_stats", "dem_status_string", "dem_destroy", "dem_find_pairs_static", "dem_set_instances"]
+            "dem_get_stats", "dem_status_string", "dem_destroy", "dem_find_pairs_static", "dem_set_instances",
+            "dem_pipe_rates"]
 MAX_INSTANCE_WALLS = 4
 
 
@@ -42,7 +44,7 @@ class Config(C.Structure):
                 ("rebuild_every", C.c_int32), ("precision", C.c_int32), ("rolling_model", C.c_int32),
                 ("n_instances", C.c_int32), ("domain_lo", C.c_double * 3), ("domain_hi", C.c_double * 3),
                 ("z_sink", C.c_double), ("max_overlap_ratio", C.c_double), ("step_block", C.c_int32),
-                ("contact_model", C.c_int32), ("integrator", C.c_int32), ("reserved1", C.c_int32),
+                ("contact_model", C.c_int32), ("integrator", C.c_int32), ("pair_eval", C.c_int32),
                 ("linear_velocity", C.c_double)]
 
 
@@ -157,6 +159,8 @@ def make_config(cfg: dict, n: int, radius_max: float, precision=None) -> Config:
     c.contact_model = int(cfg.get("contact_model", 0))
     c.integrator = int(cfg.get("integrator", 0))
     c.linear_velocity = float(cfg.get("linear_velocity", 1.0))
+    pe = cfg.get("pair_eval", "once")
+    c.pair_eval = PAIR_EVAL[pe] if isinstance(pe, str) else int(pe)
     return c
 
 
@@ -246,6 +250,22 @@ def find_pairs_static(x, cutoff: float, domain_lo, domain_hi, active=None, out=N
             _check(lib, "dem_find_pairs_static", f(xp, a, n, float(cutoff), lo, hi, C.c_void_p(res.data_ptr()),
                                                     cnt.value, C.byref(cnt), sp))
         return res[: cnt.value]
+
+
+def pipe_rates(device=None):
+    """dem_pipe_rates on `device` (default: the current one): measured thread-level
+    instructions per second of FP64 FMA, FP64 add, FP32 FMA and FP32 -> FP64 conversion."""
+    import torch
+
+    lib = load_library()
+    f = lib.dem_pipe_rates
+    f.argtypes = [C.c_void_p, C.c_void_p]
+    f.restype = C.c_int32
+    out = (C.c_double * 4)()
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        _check(lib, "dem_pipe_rates", f(out, C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
+    return {"dfma": out[0], "dadd": out[1], "ffma": out[2], "f2d": out[3]}
 
 
 def history_arrays(pairs, dt_pair, dt_wall, n: int, n_walls: int):

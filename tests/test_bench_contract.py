@@ -64,12 +64,22 @@ def test_measured_peak_is_the_copy_bandwidth():
         assert peak == bench.FALLBACK_HBM_GBS and kind == "fallback"
 
 
-def test_recorded_traffic_scales_per_particle_and_needs_the_workload():
-    t = bench.recorded_traffic("silo-packed", 4_300_000)
-    if t is None:
-        pytest.skip("no traffic line for the current step-kernel sources")
-    assert t == pytest.approx(bench.recorded_traffic("silo-packed", 2_150_000) * 2.0)
-    assert bench.recorded_traffic("drum", 4_300_000) is None
+def test_recorded_traffic_scales_per_particle_and_needs_the_workload(tmp_path, monkeypatch):
+    """A traffic line is used only for its kernel, its workload and the current sources'
+    hash, and scales with the particle count."""
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# kernel workload sha bytes particles\n"
+        "k_pair_mixed+k_int_mixed silo-packed abc123 4300000000 4300000\n"
+        "k_step_mixed silo-packed abc123 8600000000 4300000\n"
+        "k_step_mixed drum oldsha 1 1\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "sources_sha", lambda: "abc123")
+    t = bench.recorded_traffic("k_pair_mixed+k_int_mixed", "silo-packed", 2_150_000)
+    assert t == pytest.approx(2_150_000 * 1000.0)
+    assert bench.recorded_traffic("k_step_mixed", "silo-packed", 4_300_000) == pytest.approx(8.6e9)
+    assert bench.recorded_traffic("k_step_mixed", "drum", 1) is None          # taken on other sources
+    assert bench.recorded_traffic("k_pair_mixed+k_int_mixed", "dam-break", 10) is None
 
 
 def test_algorithmic_bytes_per_unit():

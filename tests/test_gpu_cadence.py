@@ -17,10 +17,11 @@ from gpu_helpers import make_gpu
 pytestmark = pytest.mark.gpu
 
 
-def run(precision, skin_over_dmax, steps):
+def run(precision, skin_over_dmax, steps, pair_eval="once"):
     wl = workloads.drum(n=2500, seed=4301, omega=3.0, precision=precision)
     wl.cfg["dt"] = 1e-5
     wl.cfg["skin"] = skin_over_dmax * 2.0 * float(wl.radius.max())
+    wl.cfg["pair_eval"] = pair_eval
     g = make_gpu(wl, precision)
     g.step(steps)
     x, v, w, act = g.state()
@@ -30,12 +31,14 @@ def run(precision, skin_over_dmax, steps):
     return digest, st
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_trajectory_is_independent_of_the_search_cadence(precision):
+@pytest.mark.parametrize("precision,pair_eval", [("mixed", "once"), ("mixed", "both"), ("fp64", "both")])
+def test_trajectory_is_independent_of_the_search_cadence(precision, pair_eval):
+    """Mixed precision with each pair evaluated once (the owner's reaction handed to the
+    partner through its record slot) and from both sides; FP64 (both sides)."""
     steps = 8000
-    a, sa = run(precision, 0.3, steps)
-    b, sb = run(precision, 0.45, steps)
-    print(precision, "searches", sa["rebuilds"], sb["rebuilds"], "inner", sa["inner_builds"], sb["inner_builds"],
+    a, sa = run(precision, 0.3, steps, pair_eval)
+    b, sb = run(precision, 0.45, steps, pair_eval)
+    print(precision, pair_eval, "searches", sa["rebuilds"], sb["rebuilds"], "inner", sa["inner_builds"], sb["inner_builds"],
           "touching", sa["n_touch"])
     assert sa["rebuilds"] != sb["rebuilds"]           # the cadences really differ
     assert sa["n_touch"] > 1000                        # and the drum is full of contacts

@@ -202,7 +202,8 @@ def test_eager_launch_equals_graph_launch():
 
 
 @pytest.mark.parametrize("maker", ["dense", "drum", "silo"])
-def test_mixed_one_step_forces_within_tolerance(maker):
+@pytest.mark.parametrize("pair_eval", ["once", "both"])
+def test_mixed_one_step_forces_within_tolerance(maker, pair_eval):
     if maker == "dense":
         wl = dense(n=2000, seed=31)
     elif maker == "drum":
@@ -210,6 +211,7 @@ def test_mixed_one_step_forces_within_tolerance(maker):
     else:
         wl = workloads.silo(n=2500, seed=3003, R=0.04, orifice=0.012, height=0.2, precision="mixed",
                             spacing=0.995, jitter=0.002)
+    wl.cfg["pair_eval"] = pair_eval
     g, o = make_gpu(wl, "mixed"), make_oracle(wl)
     if maker == "dense":
         with_history(wl, g, o)
@@ -220,7 +222,7 @@ def test_mixed_one_step_forces_within_tolerance(maker):
     gvec = wl.cfg["gravity"]
     ef = force_error(Fg, Fo, Fa, m, gvec)
     em = torque_error(Mg, Mo, Ma, m, wl.radius.astype(float), gvec)
-    print(f"mixed one-step relative error: force {ef:.3e}, torque {em:.3e}")
+    print(f"mixed ({pair_eval}) one-step relative error: force {ef:.3e}, torque {em:.3e}")
     assert ef <= MIXED_TOL and em <= MIXED_TOL
     assert Fa.sum() > 0
     # one step later positions and velocities differ by the force error integrated over dt
@@ -377,3 +379,34 @@ def test_full_size_drum_sampled():
     # constant rolling model turns rounding noise into spins (test_model_properties.py)
     sampled_parity(workloads.drum(precision="fp64", spacing=0.999), "fp64", steps=4)
     sampled_parity(workloads.drum(precision="mixed", spacing=0.999, spin=1.0), "mixed", steps=4)
+
+
+def test_mixed_pair_once_equals_both_sides_up_to_the_order_of_the_sums():
+    """Evaluating each touching pair once (by the partner of smaller id, its reaction handed
+    to the other) or from both sides applies the same law to the same pairs: the tangential
+    overlaps after an evaluation are bit-identical, the pair sets and contact counts equal,
+    and the force sums differ only by the order of FP32 additions."""
+    wl = dense(n=3000, seed=41, speed=1.0)
+    runs = {}
+    for mode in ("once", "both"):
+        wl.cfg["pair_eval"] = mode
+        g, o = make_gpu(wl, "mixed"), make_oracle(wl)
+        with_history(wl, g, o)
+        runs[mode] = (g, g.forces(), g.history(), g.pairs(), g.stats())
+    Fa, Ma = o.force_scales()
+    m = masses(wl)
+    gvec = wl.cfg["gravity"]
+    (g1, (F1, M1), h1, p1, s1), (g2, (F2, M2), h2, p2, s2) = runs["once"], runs["both"]
+    assert np.array_equal(p1, p2)
+    assert np.array_equal(h1[0], h2[0]) and np.array_equal(h1[1], h2[1]) and np.array_equal(h1[2], h2[2])
+    assert s1["n_touch"] == s2["n_touch"] > 1000 and s1["n_wall_touch"] == s2["n_wall_touch"]
+    ef = force_error(F1, F2, Fa, m, gvec)
+    em = torque_error(M1, M2, Ma, m, wl.radius.astype(float), gvec)
+    print(f"once vs both: force {ef:.2e} torque {em:.2e}")
+    assert ef <= 1e-6 and em <= 1e-6
+    for g in (g1, g2):
+        g.step(50)
+    x1, v1, _, a1 = g1.state()
+    x2, v2, _, a2 = g2.state()
+    assert np.array_equal(a1, a2)
+    assert np.abs(x1 - x2).max() < 1e-9
