@@ -127,7 +127,7 @@ dem_status derive(const dem_config* c, Derived* d) {
 
 struct Offsets {
   size_t x[2], v[2], w[2], act[2], rad[2], id[2], mask[2], hist[2], shadow[2], render[2], inst[2], itab, xref, nbr, nbr_cnt,
-      nbr_lo, inner_lo, inner_m, rec, upart,
+      nbr_lo, inner_lo, pslot, rec, upart,
       inner, inner_j, inner_cnt, xin, key, local, members, order,
       cell_count, cell_start, scan_tmp, hkey, hval, wall_tmp, wall_tmp_mask, out_v, out_w, out_F, out_M,
       stage, ctl, io_cnt, io_off;
@@ -168,7 +168,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
     // one evaluation per pair: partner positions, pushed reactions, owners' own sums
     const bool once = mixed && c->pair_eval == DEM_PAIR_EVAL_ONCE;
     o.inner_lo = L.add(once ? n : 0);
-    o.inner_m = L.add(once ? n * kInnerMax : 0);
+    o.pslot = L.add(once ? n * kInnerMax * 8 : 0);
     o.rec = L.add(once ? n * kInnerMax * 32 : 0);
     o.upart = L.add(once ? n * 32 : 0);
   }
@@ -849,7 +849,7 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   P.nbr_lo = (uint8_t*)(base + o.nbr_lo);
   P.pair_once = (cfg->precision == DEM_PRECISION_MIXED && cfg->pair_eval == DEM_PAIR_EVAL_ONCE) ? 1 : 0;
   P.inner_lo = (uint8_t*)(base + o.inner_lo);
-  P.inner_m = (uint8_t*)(base + o.inner_m);
+  P.pslot = (int2*)(base + o.pslot);
   P.rec = (float4*)(base + o.rec);
   P.upart = (float4*)(base + o.upart);
   P.inner = (uint8_t*)(base + o.inner);

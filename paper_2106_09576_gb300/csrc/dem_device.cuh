@@ -25,9 +25,10 @@
 //                                     list whose partner was within R_i + R_j + delta at the
 //                                     last inner build, ascending (so in partner-id order)
 //     inner_j           int32 [n][32] (mixed path) the partners of those slots
-//     inner_lo, inner_m uint8 [n], [n][32] (mixed path, one evaluation per pair): the
-//                                     leading slots whose partner has the smaller id, and
-//                                     for the other slots the own position in the partner's row
+//     inner_lo, pslot   uint8 [n], int2 [n][32] (mixed path, one evaluation per pair): the
+//                                     leading slots whose partner has the smaller id, and the
+//                                     other (owned) slots packed as {j, k | m << 8}, m the own
+//                                     position in the partner's row
 //     rec, upart        float4 [32][n][2], [2][n] (same): reactions pushed by owners to
 //                                     their partners, and each owner's own partial sums
 //     xin               FP32 [7][n]   (mixed path) positions at the last inner build, hi
@@ -201,12 +202,13 @@ struct Params {
   uint8_t* inner_cnt;   // [n]
   // one evaluation per pair (mixed path, pair_once): the pair belongs to its partner of
   // smaller id (the owner).  inner_lo: leading slots of a particle's inner list whose
-  // partners own the pair; inner_m: for an owned slot, where the owner sits in the
+  // partners own the pair; pslot: the owned slots, each with where the owner sits in the
   // partner's inner list; rec: slot-major [kInnerMax][n][2] the reaction an owner
   // computed for its partner {F, M_x}{M_y, M_z, 0, 0}; upart [2][n]: the owner's own sum
   // of its owned pairs and walls, same packing
   uint8_t* inner_lo;    // [n]
-  uint8_t* inner_m;     // [n][kInnerMax]
+  int2* pslot;          // [n][kInnerMax] the owned slots, packed from entry 0:
+                        //   {partner j, fine-list slot k | (position m in j's inner list) << 8}
   float4* rec;
   float4* upart;
   float* xin;           // [7][n]

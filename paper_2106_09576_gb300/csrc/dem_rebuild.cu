@@ -488,16 +488,18 @@ __global__ void k_inner_build(Params P) {
 
 // One evaluation per pair: for every slot of a particle's inner list whose pair it owns
 // (partner of larger id), the position of the particle in the partner's inner list, where
-// the step pushes the reaction.  The inner test is symmetric (the same FP32 operations on
-// both sides), so the partner's row holds the owner among its leading, foreign-owned
-// slots; a row truncated at kInnerMax has already raised the capacity error, and a slot
-// whose owner is not found is marked 255 and never written.
+// the step pushes the reaction; the owned slots are packed from entry 0 as {j, k | m << 8}
+// so that the step reads one 8-byte entry per owned pair.  The inner test is symmetric
+// (the same FP32 operations on both sides), so the partner's row holds the owner among
+// its leading, foreign-owned slots; a row truncated at kInnerMax has already raised the
+// capacity error, and a slot whose owner is not found is marked m = 255 and never written.
 __global__ void k_inner_mirror(Params P) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= P.ctl->n_act_sorted) return;
   const int cnt = P.inner_cnt[q], lo = P.inner_lo[q];
+  const uint8_t* row = P.inner + (size_t)q * kInnerMax;
   const int* rowj = P.inner_j + (size_t)q * kInnerMax;
-  uint8_t* mrow = P.inner_m + (size_t)q * kInnerMax;
+  int2* ps = P.pslot + (size_t)q * kInnerMax;
   bool missing = false;
   for (int s = lo; s < cnt; s++) {
     const int j = rowj[s];
@@ -510,7 +512,7 @@ __global__ void k_inner_mirror(Params P) {
         break;
       }
     missing |= m == 255;
-    mrow[s] = (uint8_t)m;
+    ps[s - lo] = make_int2(j, (int)row[s] | (m << 8));
   }
   if (missing) atomicOr(&P.ctl->status, kStCapacity);
 }

@@ -378,7 +378,7 @@ __device__ __forceinline__ void put_rec(const Params& P, int m, int j, const flo
 }
 
 template <bool kBatch, bool kExt>
-__global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_constant__ Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, hc = C->hc;
   const bool init = C->init != 0, last = C->last != 0;
@@ -387,22 +387,26 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   StepStats st = {0u, 0u, 0u, 0.0f, 0u};
   const double* X = P.x[cur];
-  const float4* SH = P.shadow[cur];
-  const float4* RD = P.render[cur];
+  // read-only in this kernel: the compiler may issue these loads ahead of the stores
+  const float4* __restrict__ SH = P.shadow[cur];
+  const float4* __restrict__ RD = P.render[cur];
   if (i < nact) {
     const int icnt = P.inner_cnt[i], ilo = P.inner_lo[i];
-    const uint8_t* irow = P.inner + (size_t)i * kInnerMax;
-    const uint8_t* mrow = P.inner_m + (size_t)i * kInnerMax;
-    const int* jrow = P.inner_j + (size_t)i * kInnerMax;
-    const float4 o0 = SH[i];
-    const float4 o1 = RD[3 * (size_t)i];
+    const int nown = icnt - ilo;
+    const int2* __restrict__ ps = P.pslot + (size_t)i * kInnerMax;
+    // the first owned slot is fetched with the own data, each next one during the
+    // current pair's arithmetic
+    int2 e = nown > 0 ? __ldg(ps) : make_int2(0, 0);
+    const float4 o0 = __ldg(SH + i);
+    const float4 o1 = __ldg(RD + 3 * (size_t)i);
     const float zero[3] = {0.f, 0.f, 0.f};
     float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
     if (o1.w == 0.0f) {
       // out of the system: its pairs exert nothing, and its partners' records say so
-      for (int s = ilo; s < icnt; s++) {
-        const int m = mrow[s];
-        if (m != 255) put_rec(P, m, jrow[s], zero, zero);
+      for (int t = 0; t < nown; t++) {
+        const int2 f = __ldg(ps + t);
+        const int m = (f.y >> 8) & 0xFF;
+        if (m != 255) put_rec(P, m, f.x, zero, zero);
       }
       P.mask[hc ^ 1][i] = 0ull;
     } else {
@@ -410,29 +414,30 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
       const float Rif = o0.w;
       const InstDev* I = kBatch ? P.itab + P.inst[C->sbuf][i] : nullptr;
       const MatF& Mt = kBatch ? I->mf : P.mf;
-      const float4 o2 = RD[3 * (size_t)i + 1], o3 = RD[3 * (size_t)i + 2];
+      const float4 o2 = __ldg(RD + 3 * (size_t)i + 1), o3 = __ldg(RD + 3 * (size_t)i + 2);
       const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
-      const unsigned long long mold = P.mask[hc][i];
-      const double* Hold = P.hist[hc] + (size_t)i * kHistStride * 3;
+      const unsigned long long mold = __ldg(P.mask[hc] + i);
+      const double* __restrict__ Hold = P.hist[hc] + (size_t)i * kHistStride * 3;
       double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHistStride * 3;
       const float mif = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rif * Rif * Rif;
       const float dtf = P.f_dt;
       unsigned long long mnew = 0ull;
       int rank = 0;
-      for (int s = ilo; s < icnt; s++) {
-        const int k = irow[s];
-        const int j = jrow[s];
-        const int m = mrow[s];
-        const float4 r0 = SH[j];
+      for (int t = 0; t < nown; t++) {
+        const int j = e.x;
+        const int k = e.y & 0xFF;
+        const int m = (e.y >> 8) & 0xFF;
+        const float4 r0 = __ldg(SH + j);
         const float4* rj = RD + 3 * (size_t)j;
-        const float4 r1 = rj[0], r2 = rj[1], r3 = rj[2];
+        const float4 r1 = __ldg(rj), r2 = __ldg(rj + 1), r3 = __ldg(rj + 2);
         double H[3] = {0.0, 0.0, 0.0};
         if ((mold >> k) & 1ull) {
           const int ro = __popcll(mold & ((1ull << k) - 1ull));
-          H[0] = Hold[ro * 3];
-          H[1] = Hold[ro * 3 + 1];
-          H[2] = Hold[ro * 3 + 2];
+          H[0] = __ldg(Hold + ro * 3);
+          H[1] = __ldg(Hold + ro * 3 + 1);
+          H[2] = __ldg(Hold + ro * 3 + 2);
         }
+        if (t + 1 < nown) e = __ldg(ps + t + 1);
         float rf[3] = {0.f, 0.f, 0.f}, rm[3] = {0.f, 0.f, 0.f};
         bool touch = false;
         float Rjf = 0.f, D = 0.f, Sh = 0.f, Ah = 0.f, Al = 0.f;
@@ -443,15 +448,15 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
           df_diff(hx[1], lx[1], r0.y, r1.y, s3[1], t3[1]);
           df_diff(hx[2], lx[2], r0.z, r1.z, s3[2], t3[2]);
           // S^2 - r^2 as an exact double-float
-          float p2, pe, e;
+          float p2, pe, e2;
           two_prod(s3[0], s3[0], Ah, pe);
           Al = pe + (2.0f * s3[0] + t3[0]) * t3[0];
           two_prod(s3[1], s3[1], p2, pe);
-          two_sum(Ah, p2, Ah, e);
-          Al += e + pe + (2.0f * s3[1] + t3[1]) * t3[1];
+          two_sum(Ah, p2, Ah, e2);
+          Al += e2 + pe + (2.0f * s3[1] + t3[1]) * t3[1];
           two_prod(s3[2], s3[2], p2, pe);
-          two_sum(Ah, p2, Ah, e);
-          Al += e + pe + (2.0f * s3[2] + t3[2]) * t3[2];
+          two_sum(Ah, p2, Ah, e2);
+          Al += e2 + pe + (2.0f * s3[2] + t3[2]) * t3[2];
           float Sl, P2, P2e, Dh, De;
           two_sum(Rif, Rjf, Sh, Sl);
           two_prod(Sh, Sh, P2, P2e);
@@ -581,9 +586,10 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
     }
   }
   if (i < nact) {
-    const float4 o0 = SH[i];
-    const float4 o1 = RD[3 * (size_t)i];
-    if (o1.w == 0.0f) {
+    // the in-system flag and the radius from their own arrays (the FP32 copies hold the
+    // same values): 5 bytes instead of two 16-byte vectors
+    if (P.act[cur][i] == 0) {
+      const float4 o0 = SH[i];
       for (int d = 0; d < 3; d++) {
         const double xv = X[d * n + i], vv = V[d * n + i], wv = W[d * n + i];
         P.x[nxt][d * n + i] = xv;
@@ -600,7 +606,7 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
       SHo[i] = o0;
       for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
     } else {
-      const float Rif = o0.w;
+      const float Rif = P.rad[C->sbuf][i];
       // reactions pushed by the owners of the leading slots, in partner-id order
       const int ilo = P.inner_lo[i];
       float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
