@@ -48,6 +48,8 @@ constexpr int kMaxWalls = 8;
 constexpr int kMaxNbr = 56;      // slots per particle in the fine-search list
 constexpr int kHistStride = 32;  // simultaneous contacts per particle (particles + walls)
 constexpr int kInnerMax = 32;    // entries of a particle's inner list (mixed path)
+constexpr int kHv = 4;           // doubles per stored tangential overlap: 3 components and a
+                                 // pad, so that an overlap is one whole 32-byte sector
 constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
 
 // status bits (sticky, in Control::status)
