@@ -340,7 +340,7 @@ __global__ void k_io_emit(Params P, const int* off, long long lo, long long hi, 
   const int a = ids[p];
   const int* nb = P.nbr + (size_t)p * kMaxNbr;
   const unsigned long long m = P.mask[C->hc][p];
-  const double* H = P.hist[C->hc] + (size_t)p * kHistStride * kHv;
+  const double* H = P.hist[C->hc] + (size_t)p * kHv;
   for (int k = 0; k < P.nbr_cnt[p]; k++) {
     const bool has = (m >> k) & 1ull;
     if (mode == 1 && !has) continue;
@@ -351,9 +351,9 @@ __global__ void k_io_emit(Params P, const int* off, long long lo, long long hi, 
       pairs[2 * (g - lo) + 1] = b;
       if (mode == 1) {
         const int r = __popcll(m & ((1ull << k) - 1ull));
-        vals[3 * (g - lo)] = H[kHv * r];
-        vals[3 * (g - lo) + 1] = H[kHv * r + 1];
-        vals[3 * (g - lo) + 2] = H[kHv * r + 2];
+        vals[3 * (g - lo)] = H[hrow(P.n, r)];
+        vals[3 * (g - lo) + 1] = H[hrow(P.n, r) + 1];
+        vals[3 * (g - lo) + 2] = H[hrow(P.n, r) + 2];
       }
     }
     g++;
@@ -367,15 +367,15 @@ __global__ void k_out_wall_hist(Params P, double* dst, int nw) {
   const Control* C = P.ctl;
   const int u = P.id[C->sbuf][p];
   const unsigned long long m = (p < C->n_act_sorted) ? P.mask[C->hc][p] : 0ull;
-  const double* H = P.hist[C->hc] + (size_t)p * kHistStride * kHv;
+  const double* H = P.hist[C->hc] + (size_t)p * kHv;
   for (int w = 0; w < nw; w++) {
     const int bit = kMaxNbr + w;
     double v[3] = {0.0, 0.0, 0.0};
     if ((m >> bit) & 1ull) {
       const int r = __popcll(m & ((1ull << bit) - 1ull));
-      v[0] = H[kHv * r];
-      v[1] = H[kHv * r + 1];
-      v[2] = H[kHv * r + 2];
+      v[0] = H[hrow(P.n, r)];
+      v[1] = H[hrow(P.n, r) + 1];
+      v[2] = H[hrow(P.n, r) + 2];
     }
     for (int d = 0; d < 3; d++) dst[((size_t)u * nw + w) * 3 + d] = v[d];
   }

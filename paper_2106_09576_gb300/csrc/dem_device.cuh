@@ -50,6 +50,12 @@ constexpr int kHistStride = 32;  // simultaneous contacts per particle (particle
 constexpr int kInnerMax = 32;    // entries of a particle's inner list (mixed path)
 constexpr int kHv = 4;           // doubles per stored tangential overlap: 3 components and a
                                  // pad, so that an overlap is one whole 32-byte sector
+
+// Tangential overlaps are stored in planes: entry r of every particle's compact list lies in
+// plane r, [kHistStride][n][kHv] doubles, so a warp's reads and writes of its particles'
+// r-th entries are one contiguous run (particles hold a few entries; the first planes are
+// dense).  Entry r of particle i: hist + i * kHv + hrow(n, r).
+__host__ __device__ __forceinline__ size_t hrow(int n, int r) { return (size_t)r * (size_t)n * kHv; }
 constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
 
 // status bits (sticky, in Control::status)
