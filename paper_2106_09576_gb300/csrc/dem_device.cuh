@@ -25,7 +25,7 @@
 //                                     list whose partner was within R_i + R_j + delta at the
 //                                     last inner build, ascending (so in partner-id order)
 //     inner_j           int32 [n][32] (mixed path) the partners of those slots
-//     inner_lo, pslot   uint8 [n], int2 [n][32] (mixed path, one evaluation per pair): the
+//     inner_lo, pslot   uint8 [n], int2 [32][n] (mixed path, one evaluation per pair): the
 //                                     leading slots whose partner has the smaller id, and the
 //                                     other (owned) slots packed as {j, k | m << 8}, m the own
 //                                     position in the partner's row
@@ -215,7 +215,7 @@ struct Params {
   // computed for its partner {F, M_x}{M_y, M_z, 0, 0}; upart [2][n]: the owner's own sum
   // of its owned pairs and walls, same packing
   uint8_t* inner_lo;    // [n]
-  int2* pslot;          // [n][kInnerMax] the owned slots, packed from entry 0:
+  int2* pslot;          // [kInnerMax][n] the owned slots, packed from entry 0 (slot-major):
                         //   {partner j, fine-list slot k | (position m in j's inner list) << 8}
   float4* rec;
   float4* upart;

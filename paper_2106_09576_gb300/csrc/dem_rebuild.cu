@@ -501,7 +501,7 @@ __global__ void k_inner_mirror(Params P) {
   const int cnt = P.inner_cnt[q], lo = P.inner_lo[q];
   const uint8_t* row = P.inner + (size_t)q * kInnerMax;
   const int* rowj = P.inner_j + (size_t)q * kInnerMax;
-  int2* ps = P.pslot + (size_t)q * kInnerMax;
+  int2* ps = P.pslot + q;   // slot-major: entry t at ps[t * n]
   bool missing = false;
   for (int s = lo; s < cnt; s++) {
     const int j = rowj[s];
@@ -514,7 +514,7 @@ __global__ void k_inner_mirror(Params P) {
         break;
       }
     missing |= m == 255;
-    ps[s - lo] = make_int2(j, (int)row[s] | (m << 8));
+    ps[(size_t)(s - lo) * P.n] = make_int2(j, (int)row[s] | (m << 8));
   }
   if (missing) atomicOr(&P.ctl->status, kStCapacity);
 }

@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
   if (i < nact) {
     const int icnt = P.inner_cnt[i], ilo = P.inner_lo[i];
     const int nown = icnt - ilo;
-    const int2* __restrict__ ps = P.pslot + (size_t)i * kInnerMax;
+    const int2* __restrict__ ps = P.pslot + i;   // entry t at ps[t * n]: slot-major
     // the first owned slot is fetched with the own data, each next one during the
     // current pair's arithmetic
     int2 e = nown > 0 ? __ldg(ps) : make_int2(0, 0);
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
     if (o1.w == 0.0f) {
       // out of the system: its pairs exert nothing, and its partners' records say so
       for (int t = 0; t < nown; t++) {
-        const int2 f = __ldg(ps + t);
+        const int2 f = __ldg(ps + (size_t)t * n);
         const int m = (f.y >> 8) & 0xFF;
         if (m != 255) put_rec(P, m, f.x, zero, zero);
       }
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
           H[1] = h01.y;
           H[2] = __ldg(Hold + hrow(P.n, ro) + 2);
         }
-        if (t + 1 < nown) e = __ldg(ps + t + 1);
+        if (t + 1 < nown) e = __ldg(ps + (size_t)(t + 1) * n);
         float rf[3] = {0.f, 0.f, 0.f}, rm[3] = {0.f, 0.f, 0.f};
         bool touch = false;
         float Rjf = 0.f, D = 0.f, Sh = 0.f, Ah = 0.f, Al = 0.f;
