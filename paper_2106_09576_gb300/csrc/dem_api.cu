@@ -147,7 +147,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
     o.rad[b] = L.add(n * 4);
     o.id[b] = L.add(n * 4);
     o.mask[b] = L.add(n * 8);
-    o.hist[b] = L.add(n * kHistStride * kHv * 8);
+    o.hist[b] = L.add(n * kHistStride * 3 * 8);
     const bool mixed = c->precision == DEM_PRECISION_MIXED;   // FP32 copies for neighbours
     o.shadow[b] = L.add(n * 16);
     o.render[b] = L.add(mixed ? n * 48 : 0);
@@ -170,7 +170,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
     o.inner_lo = L.add(once ? n : 0);
     o.pslot = L.add(once ? n * kInnerMax * 8 : 0);
     o.rec = L.add(once ? n * kInnerMax * 32 : 0);
-    o.upart = L.add(once ? n * 32 : 0);
+    o.upart = L.add(once ? n * 24 : 0);
   }
   o.key = L.add(n * 4);
   o.local = L.add(n * 4);
@@ -340,7 +340,7 @@ __global__ void k_io_emit(Params P, const int* off, long long lo, long long hi, 
   const int a = ids[p];
   const int* nb = P.nbr + (size_t)p * kMaxNbr;
   const unsigned long long m = P.mask[C->hc][p];
-  const double* H = P.hist[C->hc] + (size_t)p * kHv;
+  const double* H = P.hist[C->hc] + (size_t)p;
   for (int k = 0; k < P.nbr_cnt[p]; k++) {
     const bool has = (m >> k) & 1ull;
     if (mode == 1 && !has) continue;
@@ -351,9 +351,9 @@ __global__ void k_io_emit(Params P, const int* off, long long lo, long long hi, 
       pairs[2 * (g - lo) + 1] = b;
       if (mode == 1) {
         const int r = __popcll(m & ((1ull << k) - 1ull));
-        vals[3 * (g - lo)] = H[hrow(P.n, r)];
-        vals[3 * (g - lo) + 1] = H[hrow(P.n, r) + 1];
-        vals[3 * (g - lo) + 2] = H[hrow(P.n, r) + 2];
+        vals[3 * (g - lo)] = H[hcomp(P.n, r, 0)];
+        vals[3 * (g - lo) + 1] = H[hcomp(P.n, r, 1)];
+        vals[3 * (g - lo) + 2] = H[hcomp(P.n, r, 2)];
       }
     }
     g++;
@@ -367,15 +367,15 @@ __global__ void k_out_wall_hist(Params P, double* dst, int nw) {
   const Control* C = P.ctl;
   const int u = P.id[C->sbuf][p];
   const unsigned long long m = (p < C->n_act_sorted) ? P.mask[C->hc][p] : 0ull;
-  const double* H = P.hist[C->hc] + (size_t)p * kHv;
+  const double* H = P.hist[C->hc] + (size_t)p;
   for (int w = 0; w < nw; w++) {
     const int bit = kMaxNbr + w;
     double v[3] = {0.0, 0.0, 0.0};
     if ((m >> bit) & 1ull) {
       const int r = __popcll(m & ((1ull << bit) - 1ull));
-      v[0] = H[hrow(P.n, r)];
-      v[1] = H[hrow(P.n, r) + 1];
-      v[2] = H[hrow(P.n, r) + 2];
+      v[0] = H[hcomp(P.n, r, 0)];
+      v[1] = H[hcomp(P.n, r, 1)];
+      v[2] = H[hcomp(P.n, r, 2)];
     }
     for (int d = 0; d < 3; d++) dst[((size_t)u * nw + w) * 3 + d] = v[d];
   }
@@ -851,7 +851,7 @@ dem_status dem_create(const dem_config* cfg, const double* x, const double* v, c
   P.inner_lo = (uint8_t*)(base + o.inner_lo);
   P.pslot = (int2*)(base + o.pslot);
   P.rec = (float4*)(base + o.rec);
-  P.upart = (float4*)(base + o.upart);
+  P.upart = (float*)(base + o.upart);
   P.inner = (uint8_t*)(base + o.inner);
   P.inner_j = (int*)(base + o.inner_j);
   P.inner_cnt = (uint8_t*)(base + o.inner_cnt);

@@ -29,7 +29,7 @@
 //                                     leading slots whose partner has the smaller id, and the
 //                                     other (owned) slots packed as {j, k | m << 8}, m the own
 //                                     position in the partner's row
-//     rec, upart        float4 [32][n][2], [2][n] (same): reactions pushed by owners to
+//     rec, upart        float4 [32][n][2], float [6][n] (same): reactions pushed by owners to
 //                                     their partners, and each owner's own partial sums
 //     xin               FP32 [7][n]   (mixed path) positions at the last inner build, hi
 //                                     parts then lo parts, then the distance of that position
@@ -48,14 +48,15 @@ constexpr int kMaxWalls = 8;
 constexpr int kMaxNbr = 56;      // slots per particle in the fine-search list
 constexpr int kHistStride = 32;  // simultaneous contacts per particle (particles + walls)
 constexpr int kInnerMax = 32;    // entries of a particle's inner list (mixed path)
-constexpr int kHv = 4;           // doubles per stored tangential overlap: 3 components and a
-                                 // pad, so that an overlap is one whole 32-byte sector
-
-// Tangential overlaps are stored in planes: entry r of every particle's compact list lies in
-// plane r, [kHistStride][n][kHv] doubles, so a warp's reads and writes of its particles'
-// r-th entries are one contiguous run (particles hold a few entries; the first planes are
-// dense).  Entry r of particle i: hist + i * kHv + hrow(n, r).
-__host__ __device__ __forceinline__ size_t hrow(int n, int r) { return (size_t)r * (size_t)n * kHv; }
+// Tangential overlaps are stored in component planes: component d of entry r of every
+// particle's compact list lies in plane 3 r + d, [kHistStride][3][n] doubles, so a warp's
+// reads and writes of its particles' r-th entries are three contiguous runs of whole
+// sectors (a partly written sector costs a DRAM read before its write-back; particles hold
+// a few entries, the first planes are dense).  Component d of entry r of particle i:
+// hist + i + hcomp(n, r, d).
+__host__ __device__ __forceinline__ size_t hcomp(int n, int r, int d) {
+  return ((size_t)r * 3 + (size_t)d) * (size_t)n;
+}
 constexpr unsigned long long kEmptyKey = 0xFFFFFFFFFFFFFFFFull;
 
 // status bits (sticky, in Control::status)
@@ -212,13 +213,13 @@ struct Params {
   // smaller id (the owner).  inner_lo: leading slots of a particle's inner list whose
   // partners own the pair; pslot: the owned slots, each with where the owner sits in the
   // partner's inner list; rec: slot-major [kInnerMax][n][2] the reaction an owner
-  // computed for its partner {F, M_x}{M_y, M_z, 0, 0}; upart [2][n]: the owner's own sum
+  // computed for its partner {F, M_x}{M_y, M_z, 0, 0}; upart [6][n]: the owner's own sum
   // of its owned pairs and walls, same packing
   uint8_t* inner_lo;    // [n]
   int2* pslot;          // [kInnerMax][n] the owned slots, packed from entry 0 (slot-major):
                         //   {partner j, fine-list slot k | (position m in j's inner list) << 8}
   float4* rec;
-  float4* upart;
+  float* upart;
   float* xin;           // [7][n]
   unsigned* key;        // [n] cell key of the current (pre-sort) order
   int* local;           // [n] slot within the cell (order of the atomics)

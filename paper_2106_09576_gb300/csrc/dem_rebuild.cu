@@ -110,7 +110,7 @@ __global__ void k_hist_save(Params P) {
   if (!m) return;
   const int* ids = P.id[sb];
   const int a = ids[i];
-  const double* H = P.hist[hc] + (size_t)i * kHv;
+  const double* H = P.hist[hc] + (size_t)i;
   const int* nb = P.nbr + (size_t)i * kMaxNbr;
   int rank = 0;
   for (int k = 0; k < 64; k++) {
@@ -124,9 +124,9 @@ __global__ void k_hist_save(Params P) {
         for (unsigned probe = 0; probe <= P.hcap_mask; probe++) {
           unsigned long long prev = atomicCAS(&P.hkey[h], kEmptyKey, key);
           if (prev == kEmptyKey || prev == key) {
-            P.hval[3 * (size_t)h] = H[hrow(P.n, rank)];
-            P.hval[3 * (size_t)h + 1] = H[hrow(P.n, rank) + 1];
-            P.hval[3 * (size_t)h + 2] = H[hrow(P.n, rank) + 2];
+            P.hval[3 * (size_t)h] = H[hcomp(P.n, rank, 0)];
+            P.hval[3 * (size_t)h + 1] = H[hcomp(P.n, rank, 1)];
+            P.hval[3 * (size_t)h + 2] = H[hcomp(P.n, rank, 2)];
             done = true;
             break;
           }
@@ -137,9 +137,9 @@ __global__ void k_hist_save(Params P) {
     } else {
       const int w = k - kMaxNbr;
       double* dst = P.wall_tmp + ((size_t)a * kMaxWalls + w) * 3;
-      dst[0] = H[hrow(P.n, rank)];
-      dst[1] = H[hrow(P.n, rank) + 1];
-      dst[2] = H[hrow(P.n, rank) + 2];
+      dst[0] = H[hcomp(P.n, rank, 0)];
+      dst[1] = H[hcomp(P.n, rank, 1)];
+      dst[2] = H[hcomp(P.n, rank, 2)];
       P.wall_tmp_mask[a] |= (uint8_t)(1u << w);
     }
     rank++;
@@ -367,7 +367,7 @@ __global__ void k_hist_load(Params P) {
   const int a = ids[q];
   const int* nb = P.nbr + (size_t)q * kMaxNbr;
   const int cnt = P.nbr_cnt[q];
-  double* H = P.hist[hn] + (size_t)q * kHv;
+  double* H = P.hist[hn] + (size_t)q;
   unsigned long long m = 0ull;
   int rank = 0;
   // Only pairs that touch now can keep an overlap: the first force evaluation after this
@@ -393,10 +393,10 @@ __global__ void k_hist_load(Params P) {
       if (kk == key) {
         if (rank < kHistStride) {
           const double sg = a < b ? 1.0 : -1.0;
-          H[hrow(P.n, rank)] = sg * P.hval[3 * (size_t)h];
-          H[hrow(P.n, rank) + 1] = sg * P.hval[3 * (size_t)h + 1];
-          H[hrow(P.n, rank) + 2] = sg * P.hval[3 * (size_t)h + 2];
-          H[hrow(P.n, rank) + 3] = 0.0;   // the pad: the entry's sector is written whole
+          H[hcomp(P.n, rank, 0)] = sg * P.hval[3 * (size_t)h];
+          H[hcomp(P.n, rank, 1)] = sg * P.hval[3 * (size_t)h + 1];
+          H[hcomp(P.n, rank, 2)] = sg * P.hval[3 * (size_t)h + 2];
+          H[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           m |= 1ull << k;
           rank++;
         } else {
@@ -412,10 +412,10 @@ __global__ void k_hist_load(Params P) {
     if (!((wm >> w) & 1u)) continue;
     if (rank < kHistStride) {
       const double* src = P.wall_tmp + ((size_t)a * kMaxWalls + w) * 3;
-      H[hrow(P.n, rank)] = src[0];
-      H[hrow(P.n, rank) + 1] = src[1];
-      H[hrow(P.n, rank) + 2] = src[2];
-      H[hrow(P.n, rank) + 3] = 0.0;   // the pad: the entry's sector is written whole
+      H[hcomp(P.n, rank, 0)] = src[0];
+      H[hcomp(P.n, rank, 1)] = src[1];
+      H[hcomp(P.n, rank, 2)] = src[2];
+      H[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
       m |= 1ull << (kMaxNbr + w);
       rank++;
     } else {

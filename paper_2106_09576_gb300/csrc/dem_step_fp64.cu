@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
       P.mask[hc ^ 1][i] = 0ull;
     } else {
       const unsigned long long mold = P.mask[hc][i];
-      const double* Hold = P.hist[hc] + (size_t)i * kHv;
-      double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHv;
+      const double* Hold = P.hist[hc] + (size_t)i;
+      double* Hnew = P.hist[hc ^ 1] + (size_t)i;
       const int* nb = P.nbr + (size_t)i * kMaxNbr;
       const int cnt = P.nbr_cnt[i];
       unsigned long long mnew = 0ull;
@@ -108,9 +108,9 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
         double H[3] = {0.0, 0.0, 0.0};
         if ((mold >> k) & 1ull) {
           const int ro = __popcll(mold & ((1ull << k) - 1ull));
-          H[0] = Hold[hrow(P.n, ro)];
-          H[1] = Hold[hrow(P.n, ro) + 1];
-          H[2] = Hold[hrow(P.n, ro) + 2];
+          H[0] = Hold[hcomp(P.n, ro, 0)];
+          H[1] = Hold[hcomp(P.n, ro, 1)];
+          H[2] = Hold[hcomp(P.n, ro, 2)];
         }
         double f[3], nxFt[3], Mr[3];
         law_d(nrm, dn, vij, dw, rwxn, Re, me, Mt.Ye_pp, Mt.Ge_pp, Mt.ceta_pp, Mt.mu_pp, Mt.mur_pp, P.rolling,
@@ -122,10 +122,10 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
         st.touch++;
         st.max_ovl = fmaxf(st.max_ovl, (float)(dn / fmin(Ri, Rj)));
         if (rank < kHistStride) {
-          Hnew[hrow(P.n, rank)] = H[0];
-          Hnew[hrow(P.n, rank) + 1] = H[1];
-          Hnew[hrow(P.n, rank) + 2] = H[2];
-          Hnew[hrow(P.n, rank) + 3] = 0.0;   // the pad: the entry's sector is written whole
+          Hnew[hcomp(P.n, rank, 0)] = H[0];
+          Hnew[hcomp(P.n, rank, 1)] = H[1];
+          Hnew[hcomp(P.n, rank, 2)] = H[2];
+          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << k;
           rank++;
         } else {
@@ -148,9 +148,9 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
         double H[3] = {0.0, 0.0, 0.0};
         if ((mold >> bit) & 1ull) {
           const int ro = __popcll(mold & ((1ull << bit) - 1ull));
-          H[0] = Hold[hrow(P.n, ro)];
-          H[1] = Hold[hrow(P.n, ro) + 1];
-          H[2] = Hold[hrow(P.n, ro) + 2];
+          H[0] = Hold[hcomp(P.n, ro, 0)];
+          H[1] = Hold[hcomp(P.n, ro, 1)];
+          H[2] = Hold[hcomp(P.n, ro, 2)];
         }
         double rw[3], rwxn[3], vij[3], dw[3], rdw[3], vom[3];
         for (int d = 0; d < 3; d++) rw[d] = Ri * wi[d];
@@ -171,10 +171,10 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
         st.max_ovl = fmaxf(st.max_ovl, (float)(dn / Ri));
         st.wtouch++;
         if (rank < kHistStride) {
-          Hnew[hrow(P.n, rank)] = H[0];
-          Hnew[hrow(P.n, rank) + 1] = H[1];
-          Hnew[hrow(P.n, rank) + 2] = H[2];
-          Hnew[hrow(P.n, rank) + 3] = 0.0;   // the pad: the entry's sector is written whole
+          Hnew[hcomp(P.n, rank, 0)] = H[0];
+          Hnew[hcomp(P.n, rank, 1)] = H[1];
+          Hnew[hcomp(P.n, rank, 2)] = H[2];
+          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << bit;
           rank++;
         } else {

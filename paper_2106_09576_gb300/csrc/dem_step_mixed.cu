@@ -56,9 +56,9 @@ __device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstD
   double H[3] = {0.0, 0.0, 0.0};
   if ((mold >> bit) & 1ull) {
     const int ro = __popcll(mold & ((1ull << bit) - 1ull));
-    H[0] = Hold[hrow(P.n, ro)];
-    H[1] = Hold[hrow(P.n, ro) + 1];
-    H[2] = Hold[hrow(P.n, ro) + 2];
+    H[0] = Hold[hcomp(P.n, ro, 0)];
+    H[1] = Hold[hcomp(P.n, ro, 1)];
+    H[2] = Hold[hcomp(P.n, ro, 2)];
   }
   const float nf[3] = {(float)nrmd[0], (float)nrmd[1], (float)nrmd[2]};
   const float dnf = (float)dnd;
@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       const float4 o2 = RD[3 * (size_t)i + 1], o3 = RD[3 * (size_t)i + 2];
       const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
       const unsigned long long mold = P.mask[hc][i];
-      const double* Hold = P.hist[hc] + (size_t)i * kHv;
-      double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHv;
+      const double* Hold = P.hist[hc] + (size_t)i;
+      double* Hnew = P.hist[hc ^ 1] + (size_t)i;
       const float mif = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rif * Rif * Rif;
       const float dtf = P.f_dt;
       float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         double H[3] = {0.0, 0.0, 0.0};
         if ((mold >> k) & 1ull) {
           const int ro = __popcll(mold & ((1ull << k) - 1ull));
-          H[0] = Hold[hrow(P.n, ro)];
-          H[1] = Hold[hrow(P.n, ro) + 1];
-          H[2] = Hold[hrow(P.n, ro) + 2];
+          H[0] = Hold[hcomp(P.n, ro, 0)];
+          H[1] = Hold[hcomp(P.n, ro, 1)];
+          H[2] = Hold[hcomp(P.n, ro, 2)];
         }
         if (r1.w == 0.0f) continue;                    // partner out of the system
         const float Rjf = r0.w;
@@ -231,10 +231,10 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         st.touch++;
         st.max_ovl = fmaxf(st.max_ovl, dn / fminf(Rif, Rjf));
         if (rank < kHistStride) {
-          Hnew[hrow(P.n, rank)] = H[0];
-          Hnew[hrow(P.n, rank) + 1] = H[1];
-          Hnew[hrow(P.n, rank) + 2] = H[2];
-          Hnew[hrow(P.n, rank) + 3] = 0.0;   // the pad: the entry's sector is written whole
+          Hnew[hcomp(P.n, rank, 0)] = H[0];
+          Hnew[hcomp(P.n, rank, 1)] = H[1];
+          Hnew[hcomp(P.n, rank, 2)] = H[2];
+          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << k;
           rank++;
         } else {
@@ -275,10 +275,10 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         st.max_ovl = fmaxf(st.max_ovl, o.ovl);
         st.wtouch++;
         if (rank < kHistStride) {
-          Hnew[hrow(P.n, rank)] = o.H[0];
-          Hnew[hrow(P.n, rank) + 1] = o.H[1];
-          Hnew[hrow(P.n, rank) + 2] = o.H[2];
-          Hnew[hrow(P.n, rank) + 3] = 0.0;   // the pad: the entry's sector is written whole
+          Hnew[hcomp(P.n, rank, 0)] = o.H[0];
+          Hnew[hcomp(P.n, rank, 1)] = o.H[1];
+          Hnew[hcomp(P.n, rank, 2)] = o.H[2];
+          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << (kMaxNbr + k);
           rank++;
         } else {
@@ -419,8 +419,8 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
       const float4 o2 = __ldg(RD + 3 * (size_t)i + 1), o3 = __ldg(RD + 3 * (size_t)i + 2);
       const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
       const unsigned long long mold = __ldg(P.mask[hc] + i);
-      const double* __restrict__ Hold = P.hist[hc] + (size_t)i * kHv;
-      double* Hnew = P.hist[hc ^ 1] + (size_t)i * kHv;
+      const double* __restrict__ Hold = P.hist[hc] + (size_t)i;
+      double* Hnew = P.hist[hc ^ 1] + (size_t)i;
       const float mif = P.f_density * (4.0f / 3.0f) * 3.14159265358979f * Rif * Rif * Rif;
       const float dtf = P.f_dt;
       unsigned long long mnew = 0ull;
@@ -435,11 +435,9 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
         double H[3] = {0.0, 0.0, 0.0};
         if ((mold >> k) & 1ull) {
           const int ro = __popcll(mold & ((1ull << k) - 1ull));
-          // one 32-byte entry: two 16-byte loads
-          const double2 h01 = __ldg(reinterpret_cast<const double2*>(Hold + hrow(P.n, ro)));
-          H[0] = h01.x;
-          H[1] = h01.y;
-          H[2] = __ldg(Hold + hrow(P.n, ro) + 2);
+          H[0] = __ldg(Hold + hcomp(P.n, ro, 0));
+          H[1] = __ldg(Hold + hcomp(P.n, ro, 1));
+          H[2] = __ldg(Hold + hcomp(P.n, ro, 2));
         }
         if (t + 1 < nown) e = __ldg(ps + (size_t)(t + 1) * n);
         float rf[3] = {0.f, 0.f, 0.f}, rm[3] = {0.f, 0.f, 0.f};
@@ -501,9 +499,9 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
           st.touch += 2u;
           st.max_ovl = fmaxf(st.max_ovl, dn / fminf(Rif, Rjf));
           if (rank < kHistStride) {
-            // the whole 32-byte entry (pad included), so the sector is written in full
-            reinterpret_cast<double2*>(Hnew + hrow(P.n, rank))[0] = make_double2(H[0], H[1]);
-            reinterpret_cast<double2*>(Hnew + hrow(P.n, rank))[1] = make_double2(H[2], 0.0);
+            Hnew[hcomp(P.n, rank, 0)] = H[0];
+            Hnew[hcomp(P.n, rank, 1)] = H[1];
+            Hnew[hcomp(P.n, rank, 2)] = H[2];
             mnew |= 1ull << k;
             rank++;
           } else {
@@ -545,10 +543,10 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
         st.max_ovl = fmaxf(st.max_ovl, o.ovl);
         st.wtouch++;
         if (rank < kHistStride) {
-          Hnew[hrow(P.n, rank)] = o.H[0];
-          Hnew[hrow(P.n, rank) + 1] = o.H[1];
-          Hnew[hrow(P.n, rank) + 2] = o.H[2];
-          Hnew[hrow(P.n, rank) + 3] = 0.0;   // the pad: the entry's sector is written whole
+          Hnew[hcomp(P.n, rank, 0)] = o.H[0];
+          Hnew[hcomp(P.n, rank, 1)] = o.H[1];
+          Hnew[hcomp(P.n, rank, 2)] = o.H[2];
+          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << (kMaxNbr + k);
           rank++;
         } else {
@@ -557,8 +555,11 @@ __global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_const
       }
       P.mask[hc ^ 1][i] = mnew;
     }
-    P.upart[i] = make_float4(Ff[0], Ff[1], Ff[2], Mf[0]);
-    P.upart[n + i] = make_float4(Mf[1], Mf[2], 0.0f, 0.0f);
+    // six planes of n floats: a warp writes 128 contiguous bytes per plane
+    for (int d = 0; d < 3; d++) {
+      P.upart[(size_t)d * n + i] = Ff[d];
+      P.upart[(size_t)(3 + d) * n + i] = Mf[d];
+    }
   }
   if (P.max_overlap_ratio > 0.0 && st.max_ovl > (float)P.max_overlap_ratio) st.status |= kStOverlap;
   end_step(st, P.ctl, last, false);
@@ -625,13 +626,10 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
         Mf[1] += b.x;
         Mf[2] += b.y;
       }
-      const float4 u0 = P.upart[i], u1 = P.upart[n + i];
-      Ff[0] += u0.x;
-      Ff[1] += u0.y;
-      Ff[2] += u0.z;
-      Mf[0] += u0.w;
-      Mf[1] += u1.x;
-      Mf[2] += u1.y;
+      for (int d = 0; d < 3; d++) {
+        Ff[d] += P.upart[(size_t)d * n + i];
+        Mf[d] += P.upart[(size_t)(3 + d) * n + i];
+      }
 
       // ---------------- velocity Verlet in FP64 with FP32 accelerations (Eqs. main1, main2),
       // or explicit Euler (Eq. integ_EE: x^{n+1} = x^n + v^n dt, v^{n+1} = v^n + a^n dt)
