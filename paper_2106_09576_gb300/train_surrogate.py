@@ -1,6 +1,8 @@
 """Trains the drum surrogate on DEM trajectories and compares it with plain DEM.
 
     python -m paper_2106_09576_gb300.train_surrogate [--trajectories 200] [--eval-steps 50000]
+    python -m paper_2106_09576_gb300.train_surrogate --particles 20000 --train-settle 20000 \
+        --eval-particles 200000 --settle 100000 --eval-drums 1   # trained on 20k drums, judged on 200k
 
 1. 200 seeded DEM trajectories of small drums (the 200k drum's materials, radii and speed)
    give (state, increments over 10 steps) samples, the input velocities and spins perturbed
@@ -38,6 +40,11 @@ def main():
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--eval-steps", type=int, default=50000)
     ap.add_argument("--eval-drums", type=int, default=3)
+    ap.add_argument("--eval-particles", type=int, default=None,
+                    help="spheres of the evaluation drums (default: --particles); the network's inputs "
+                         "are per sphere and per contact, so a model trained on small drums runs on large ones")
+    ap.add_argument("--settle", type=int, default=20000, help="DEM steps before an evaluation rollout")
+    ap.add_argument("--train-settle", type=int, default=4000, help="DEM steps before a trajectory's first sample")
     ap.add_argument("--noise-v", type=float, default=0.1, help="input velocity noise, in velocity scales")
     ap.add_argument("--noise-x", type=float, default=0.0, help="input position noise, in diameters")
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -45,30 +52,43 @@ def main():
     ap.add_argument("--overlap-factor", type=float, default=0.0,
                     help="rollout: or this times the largest overlap of the last DEM state")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--save", default=None, help="write the trained parameters and output scale (.npz)")
+    ap.add_argument("--load", default=None, help="skip data and training: parameters from a --save file")
     a = ap.parse_args()
     dev = torch.device("cuda")
     t0 = time.perf_counter()
     net = SG.SurrogateNet()
-    train = SG.drum_trajectories(a.trajectories, a.particles, 4000, 6, 60, net, noise_v=a.noise_v,
-                                 noise_x=a.noise_x)
-    SG.fit_output_scale(net, train)
-    held = SG.drum_trajectories(a.held_out, a.particles, 4000, 6, 60, net, seed0=workloads.seed_for(5, 900))
-    t_data = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    hist = SG.train(net, train, a.epochs, lr=a.lr)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    mse, zero = SG.evaluate(net, held)
+    if a.load:
+        z = np.load(a.load)
+        net.params.copy_(torch.tensor(z["params"], device=dev))
+        net.out_scale.copy_(torch.tensor(z["out_scale"], device=dev))
+        net.sync_bf16()
+        train, hist, mse, zero, t_data, t_train = [], [], None, None, 0.0, 0.0
+    else:
+        train = SG.drum_trajectories(a.trajectories, a.particles, a.train_settle, 6, 60, net, noise_v=a.noise_v,
+                                     noise_x=a.noise_x)
+        SG.fit_output_scale(net, train)
+        held = SG.drum_trajectories(a.held_out, a.particles, a.train_settle, 6, 60, net,
+                                    seed0=workloads.seed_for(5, 900))
+        t_data = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        hist = SG.train(net, train, a.epochs, lr=a.lr)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        mse, zero = SG.evaluate(net, held)
+        if a.save:
+            np.savez(a.save, params=net.params.cpu().numpy(), out_scale=net.out_scale.cpu().numpy())
 
     rows = []
+    n_eval = a.eval_particles or a.particles
     for k in range(a.eval_drums):
-        wl = workloads.drum(n=a.particles, seed=workloads.seed_for(5, 950 + k), omega=1.0, precision="mixed",
+        wl = workloads.drum(n=n_eval, seed=workloads.seed_for(5, 950 + k), omega=1.0, precision="mixed",
                             spacing=0.999)
         L, dmax = wl.cfg["drum_length"], 2.0 * float(wl.radius.max())
         res = {}
         for mode in ("dem", "surrogate"):
             g = DEM(wl.cfg, wl.x, wl.v, wl.w, wl.radius, wl.walls, precision="mixed", device=dev)
-            g.step(20000)                                   # settle and start tumbling
+            g.step(a.settle)                                # settle and start tumbling
             torch.cuda.synchronize()
             t = time.perf_counter()
             if mode == "dem":
@@ -93,7 +113,8 @@ def main():
     ke_err = [abs(r["surrogate"]["kinetic_energy"] - r["dem"]["kinetic_energy"]) / max(r["dem"]["kinetic_energy"],
                                                                                        1e-30) for r in rows]
     speed = [r["dem"]["seconds"] / r["surrogate"]["seconds"] for r in rows]
-    out = dict(trajectories=a.trajectories, samples=len(train), particles=a.particles, epochs=a.epochs,
+    out = dict(trajectories=a.trajectories, samples=len(train), particles=a.particles, eval_particles=n_eval,
+               settle_steps=a.settle, train_settle_steps=a.train_settle, epochs=a.epochs,
                noise_v=a.noise_v, noise_x=a.noise_x, lr=a.lr, max_overlap=a.max_overlap,
                overlap_factor=a.overlap_factor,
                seconds_data=t_data, seconds_train=t_train, loss_history=hist,
