@@ -50,7 +50,10 @@ def parse():
     p.add_argument("--steps", type=int, default=1000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["silo", "drum", "dam"], default="silo")
+    p.add_argument("--workload", choices=["silo", "drum", "dam", "surrogate"], default="silo",
+                   help="surrogate: timings of the learned surrogate's kernels on the 200,000-sphere drum graph")
+    p.add_argument("--surrogate-forward", type=int, default=0,
+                   help="--workload surrogate: only run this many forward passes (for ncu)")
     p.add_argument("--n", type=int, default=None, help="override the particle count (smaller runs)")
     p.add_argument("--skin", type=float, default=None,
                    help="override the search skin, in largest diameters (analysis runs only)")
@@ -729,10 +732,87 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_surrogate(args):
+    """Timings of the surrogate's kernels at the size of the 200,000-sphere drum (CUDA events
+    after warm-up): the 128-wide product on its own, C [M][128] = A [M][K] W [K][128] with
+    M = 1,228,800 and K = 144 and 256 (BF16 in, FP32 out) -- the tcgen05 kernel of the
+    forward pass, the mma.sync kernel of the backward pass, and torch.matmul (cuBLAS, BF16
+    out) for context; bytes = M (2 K + 4 * 128) + 2 K 128 -- and the forward and backward
+    passes of the network on the radius-1.2 d graph of the drum fill (about 2.3M directed
+    edges).  One JSON line."""
+    import torch
+    import workloads
+    from paper_2106_09576_gb300 import surrogate as SG
+
+    dev = torch.device("cuda")
+    s = torch.cuda.current_stream()
+
+    def timeit(fn, reps=10, warm=3):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    wl = workloads.drum(n=200_000, precision="mixed", spacing=0.999)
+    x, v, w = (torch.tensor(a, device=dev) for a in (wl.x, wl.v, wl.w))
+    r = torch.tensor(wl.radius, device=dev)
+    net = SG.SurrogateNet()
+    t0 = time.perf_counter()
+    g = SG.Graph(x, 1.2 * 2.0 * float(wl.radius.max()), wl.cfg["domain_lo"], wl.cfg["domain_hi"])
+    torch.cuda.synchronize()
+    t_graph = time.perf_counter() - t0
+    X, E = net.features(x, v, w, r, g, SG.drum_geometry(wl, dev))
+    if args.surrogate_forward:
+        for _ in range(args.surrogate_forward):
+            Y = net.forward(X, E, g)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": "surrogate-drum-200000", "nodes": g.n, "edges": g.n_edges,
+                          "forwards": args.surrogate_forward, "checksum": float(Y.abs().sum())}))
+        return
+    out = {"workload": "surrogate-drum-200000", "nodes": g.n, "edges": g.n_edges, "graph_s": t_graph}
+    out["forward_ms"] = timeit(lambda: net.forward(X, E, g))
+    Y = net.forward(X, E, g)
+    dY = torch.randn_like(Y)
+    out["backward_ms"] = timeit(lambda: net.backward(dY, g))
+    fl = 2 * (g.n * 16 * 128 + g.n_edges * 144 * 128 + 3 * g.n * 256 * 128 + g.n * 128 * 8)
+    out["forward_gflop"] = fl / 1e9
+    del X, E, Y, dY, g
+    M, N = 1_228_800, 128
+    lib = SG.lib()
+    peak, peak_src = measured_hbm_peak()
+    for K in (144, 256):
+        A = torch.randn(M, K, device=dev).to(torch.bfloat16)
+        B = torch.randn(K, N, device=dev).to(torch.bfloat16)
+        C = torch.empty(M, N, device=dev)
+        byt = M * K * 2 + K * N * 2 + M * N * 4
+        ref = A[:4096].float() @ B.float()
+        for name, fn in (("tcgen05", lambda: lib.surr_gemm_bf16_tc(SG._p(A), SG._p(B), SG._p(C), M, K,
+                                                                     SG._stream(torch, dev))),
+                         ("mma_sync", lambda: lib.surr_gemm_bf16(SG._p(A), SG._p(B), SG._p(C), M, K, N,
+                                                                  SG._stream(torch, dev)))):
+            ms = timeit(lambda: SG._ok(name, fn()))
+            err = float((C[:4096] - ref).abs().max() / ref.abs().max())
+            out[f"{name}_K{K}"] = {"ms": ms, "tflops": 2 * M * N * K / ms / 1e9, "gbs": byt / ms / 1e6,
+                                   "frac_of_hbm": byt / ms / 1e6 / peak, "rel_err": err}
+        ms = timeit(lambda: torch.matmul(A, B))
+        out[f"cublas_bf16out_K{K}"] = {"ms": ms, "gbs": (M * K * 2 + K * N * 2 + M * N * 2) / ms / 1e6}
+        del A, B, C
+    out["hbm_peak"] = {"value": peak, "unit": "GB/s", "source": peak_src}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     else:
         run_ours(args)
 

@@ -612,10 +612,22 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
       SHo[i] = o0;
       for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
     } else {
+      // every independent load first: the FP64 state and the owner sums do not depend on
+      // the reactions, so their latencies overlap
+      double xs[3], vs[3], ws[3];
+      float us[6];
+      for (int d = 0; d < 3; d++) {
+        xs[d] = X[d * n + i];
+        vs[d] = V[d * n + i];
+        ws[d] = W[d * n + i];
+        us[d] = P.upart[(size_t)d * n + i];
+        us[3 + d] = P.upart[(size_t)(3 + d) * n + i];
+      }
       const float Rif = P.rad[C->sbuf][i];
       // reactions pushed by the owners of the leading slots, in partner-id order
       const int ilo = P.inner_lo[i];
       float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
+#pragma unroll 4
       for (int s = 0; s < ilo; s++) {
         const float4* r = P.rec + 2 * ((size_t)s * n + i);
         const float4 a = r[0], b = r[1];
@@ -627,8 +639,8 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
         Mf[2] += b.y;
       }
       for (int d = 0; d < 3; d++) {
-        Ff[d] += P.upart[(size_t)d * n + i];
-        Mf[d] += P.upart[(size_t)(3 + d) * n + i];
+        Ff[d] += us[d];
+        Mf[d] += us[3 + d];
       }
 
       // ---------------- velocity Verlet in FP64 with FP32 accelerations (Eqs. main1, main2),
@@ -638,7 +650,7 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
       const float inv_I = 1.0f / (0.4f * mif * Rif * Rif);
       double xn[3], vn[3], wn[3];
       for (int d = 0; d < 3; d++) {
-        const double xi = X[d * n + i], vi = V[d * n + i], wi = W[d * n + i];
+        const double xi = xs[d], vi = vs[d], wi = ws[d];
         const double a = f2d_int(Ff[d] * inv_m + P.f_g[d]);
         const double al = f2d_int(Mf[d] * inv_I);
         const bool euler = kExt && P.integrator == 1;
