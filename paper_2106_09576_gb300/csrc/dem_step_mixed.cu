@@ -380,7 +380,7 @@ __device__ __forceinline__ void put_rec(const Params& P, int m, int j, const flo
 }
 
 template <bool kBatch, bool kExt>
-__global__ void __launch_bounds__(kStepBlock, 5) k_pair_mixed(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_constant__ Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, hc = C->hc;
   const bool init = C->init != 0, last = C->last != 0;

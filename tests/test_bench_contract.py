@@ -7,6 +7,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -104,3 +105,34 @@ def test_clock_summary_reads_nvidia_smi_lines():
     hot = bench.ClockSampler.summarize(["0, 1200, 2070, 900, 0x40, Not Active, Active, Not Active, Not Active"])
     assert hot["reasons"] == ["hw_thermal_slowdown"]
     assert bench.ClockSampler.summarize([])["sm_mhz"] is None
+
+
+def test_recorded_pipe_counts_need_the_kernel_workload_and_sources(tmp_path, monkeypatch):
+    """The FP64 roofline's instruction count is used only for its kernel, its workload and
+    the current sources' hash, per particle."""
+    (tmp_path / "profiles").mkdir()
+    src = tmp_path / "a.cu"
+    src.write_text("kernel source")
+    import hashlib
+    sha = hashlib.sha256(b"kernel source").hexdigest()[:16]
+    (tmp_path / "profiles" / "pipe_counts.txt").write_text(
+        f"# kernel workload sha fp64 all particles\nk_step_fp64 silo-packed {sha} 600 3000 100\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    pc = bench.recorded_pipe_counts("k_step_fp64", "silo-packed", ["a.cu"])
+    assert pc == {"fp64_warp_inst_per_particle": 6.0, "warp_inst_per_particle": 30.0}
+    assert bench.recorded_pipe_counts("k_step_fp64", "drum", ["a.cu"]) is None
+    src.write_text("changed source")
+    assert bench.recorded_pipe_counts("k_step_fp64", "silo-packed", ["a.cu"]) is None
+
+
+def test_all_core_oracle_baseline_spreads_samples_and_sums_rates():
+    """The all-core CPU baseline: well-separated sample centres, one spawned single-thread
+    oracle process per core, particle-steps summed over the common wall time."""
+    import workloads
+    wl = workloads.lattice(n=3000, seed=4)
+    c = bench._spread_centres(wl.x, 4)
+    d = np.linalg.norm(c[:, None, :] - c[None, :, :], axis=2)
+    assert len(c) == 4 and d[np.triu_indices(4, 1)].min() > 0.25 * (wl.x.max(0) - wl.x.min(0)).max()
+    rate, k, steps, wall = bench.oracle_rate_all_cores(wl, 0.5, 2)
+    assert k == 2000 and steps >= 3 and wall > 0     # at least 2,000 spheres per process
+    assert rate > 0 and np.isfinite(rate)
