@@ -116,9 +116,19 @@ def test_workspace_bytes_and_validation(lib):
     c = D.make_config(cfg_dict(n_instances=4), 1000, 1.5e-3)
     s3 = C.c_size_t(0)
     assert lib.dem_workspace_bytes(C.byref(c), C.byref(s3)) == 0 and s3.value > size.value
-    for bad in (dict(n_instances=-1), dict(n_instances=2000), dict(step_block=48)):
+    for bad in (dict(n_instances=-1), dict(n_instances=2000), dict(step_block=48), dict(pair_eval=2),
+                dict(pair_eval=-1)):
         c = D.make_config(cfg_dict(**bad), 1000, 1.5e-3)
         assert lib.dem_workspace_bytes(C.byref(c), C.byref(size)) == 1
+    # one evaluation per pair needs its records and owned-slot entries (mixed contexts only)
+    sizes = {}
+    for prec in ("mixed", "fp64"):
+        for pe in ("once", "both"):
+            c = D.make_config(cfg_dict(pair_eval=pe), 1000, 1.5e-3, precision=prec)
+            sz = C.c_size_t(0)
+            assert lib.dem_workspace_bytes(C.byref(c), C.byref(sz)) == 0
+            sizes[prec, pe] = sz.value
+    assert sizes["mixed", "once"] > sizes["mixed", "both"] > sizes["fp64", "once"] == sizes["fp64", "both"]
 
 
 def test_create_rejects_null_arguments_without_touching_the_device(lib):
