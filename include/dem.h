@@ -29,6 +29,8 @@
  *     (capacity, non-finite state, excessive overlap) are sticky: they are reported by
  *     the next call that synchronises (dem_get_state, dem_get_stats, dem_sync, and
  *     dem_step when it finds the flag already set) and clear only through dem_set_state.
+ *     A capacity error is reported before the others: once a list or table has been
+ *     truncated the state that follows is not defined (it may turn non-finite).
  *   - A context is used by one host thread at a time.
  */
 #ifndef DEM_GB300_H

@@ -61,7 +61,9 @@ int surr_forward(const void* params_bf16, const float* params, const float* X, c
                  float* Y, void* stream);
 
 /* Backward pass of the last forward on the same workspace: dY [n][8] in, grad [total] out
- * (FP32, overwritten). */
+ * (FP32, overwritten).  The data gradients of the 128-wide layers (dz W^T, one 128-column
+ * block of W^T at a time) run on the 5th-generation tensor cores; the weight gradients,
+ * reductions over the node or edge dimension, on the warp-level product. */
 int surr_backward(const void* params_bf16, const float* dY, const int32_t* row_ptr, const int32_t* col,
                   int64_t n, int64_t n_edges, void* workspace, float* grad, void* stream);
 
@@ -96,7 +98,7 @@ int surr_apply(double* x, double* v, double* w, const float* radius, int64_t n, 
                const float* out_scale, double kdt, void* stream);
 
 /* C[M][N] = A[M][K] B[K][N] with A, B BF16 row-major, C FP32: the warp-level tensor-core
- * product (mma.sync) used by the backward pass and the decoder, exposed for its own test.
+ * product (mma.sync) used by the weight gradients and the decoder, exposed for its own test.
  * M any, K a multiple of 16, N a multiple of 8. */
 int surr_gemm_bf16(const void* A, const void* B, float* C, int64_t M, int64_t K, int64_t N, void* stream);
 

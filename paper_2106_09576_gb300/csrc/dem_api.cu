@@ -164,7 +164,7 @@ Offsets layout(const dem_config* c, const Derived& d) {
     o.inner = L.add(mixed ? n * kInnerMax : 0);
     o.inner_j = L.add(mixed ? n * kInnerMax * 4 : 0);
     o.inner_cnt = L.add(mixed ? n : 0);
-    o.xin = L.add(mixed ? 7 * n * 4 : 0);
+    o.xin = L.add(mixed ? 4 * n * 4 : 0);
     // one evaluation per pair: partner positions, pushed reactions, owners' own sums
     const bool once = mixed && c->pair_eval == DEM_PAIR_EVAL_ONCE;
     o.inner_lo = L.add(once ? n : 0);
@@ -450,10 +450,12 @@ dem_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DEM_OK : DEM_E
     if (e_ != cudaSuccess) return DEM_ERR_CUDA;  \
   } while (0)
 
+// A truncated list or table leaves the steps that follow undefined (a record nobody
+// wrote, a contact dropped), so the capacity error, the cause, is reported first.
 dem_status status_from_bits(unsigned b) {
+  if (b & kStCapacity) return DEM_ERR_CAPACITY;
   if (b & kStNonfinite) return DEM_ERR_NONFINITE;
   if (b & kStOverlap) return DEM_ERR_OVERLAP;
-  if (b & kStCapacity) return DEM_ERR_CAPACITY;
   if (b & kStTimeout) return DEM_ERR_TIMEOUT;
   return DEM_OK;
 }

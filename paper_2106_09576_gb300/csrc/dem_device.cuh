@@ -8,17 +8,18 @@
 //     xref              FP64 [3][n]   positions at the last contact search; in a mixed
 //                                     context FP32 [6][n]: their hi parts, then lo parts
 //     shadow[2]         float4 [n]    {hx, hy, hz, R} of each particle: written at each
-//                                     contact search (the FP32 filters of the fine search
-//                                     and the history restore read it) and, in a mixed
-//                                     context, by every step (the inner-list builds and
-//                                     the contact partners read it); ping-pong with the state
-//     render[2]         float4 [n][3] {lx, ly, lz, in-system} {vx, vy, vz, wx}
-//                                     {wy, wz, 0, 0} (mixed path): what a contact partner
-//                                     reads; x = hx + lx to 2^-48; ping-pong with the state
+//                                     contact search, read by its FP32 filters (the fine
+//                                     search and the history restore); ping-pong with the state
+//     render[2]         float4 [n][3] {hx, hy, hz, lx} {ly, lz, vx, vy} {vz, wx, wy, wz}
+//                                     (mixed path): the FP32 copy that contact partners and
+//                                     the inner-list build read, written by every step;
+//                                     x = hx + lx to 2^-48; a particle out of the system has
+//                                     hx = hy = hz = kFar; the radius is rad[]; ping-pong
+//                                     with the state
 //     mask[2]           uint64 [n]    bit k < 56: neighbour slot k has a tangential overlap;
 //                                     bit 56+w: wall w has one (parity ctl->hc)
-//     hist[2]           FP64 [n][32][3] tangential overlaps of the set bits, compact, in
-//                                     bit order (parity ctl->hc)
+//     hist[2]           FP64 [32][3][n] tangential overlaps of the set bits, compact, in
+//                                     bit order, in component planes (parity ctl->hc)
 //     nbr               int32 [n][56] fine-search list (full list: each pair twice)
 //     nbr_cnt           int32 [n]
 //     inner, inner_cnt  uint8 [n][32], uint8 [n] (mixed path): the slots of the fine-search
@@ -48,6 +49,9 @@ constexpr int kMaxWalls = 8;
 constexpr int kMaxNbr = 56;      // slots per particle in the fine-search list
 constexpr int kHistStride = 32;  // simultaneous contacts per particle (particles + walls)
 constexpr int kInnerMax = 32;    // entries of a particle's inner list (mixed path)
+// Position of a particle out of the system in the FP32 copies of the mixed path: its
+// square (1e36) is still finite in FP32.
+constexpr float kFar = 1e18f;
 // Tangential overlaps are stored in component planes: component d of entry r of every
 // particle's compact list lies in plane 3 r + d, [kHistStride][3][n] doubles, so a warp's
 // reads and writes of its particles' r-th entries are three contiguous runs of whole
@@ -202,7 +206,7 @@ struct Params {
   double* hist[2];
   double* xref;
   float4* shadow[2];    // [n] FP32 {x_hi, R} (see the layout above)
-  float4* render[2];    // [n][3] FP32 {x_lo, flag} {v, w_x} {w_y, w_z, 0, 0}
+  float4* render[2];    // [n][3] FP32 {x_hi, x_lo.x} {x_lo.y, x_lo.z, v.x, v.y} {v.z, w}
   int* nbr;
   int* nbr_cnt;
   uint8_t* nbr_lo;      // [n] entries of the fine-search list with a smaller partner id
@@ -220,7 +224,7 @@ struct Params {
                         //   {partner j, fine-list slot k | (position m in j's inner list) << 8}
   float4* rec;
   float* upart;
-  float* xin;           // [7][n]
+  float* xin;           // [4][n] hi parts of x at the last inner refresh, and |x_in - x_ref|
   unsigned* key;        // [n] cell key of the current (pre-sort) order
   int* local;           // [n] slot within the cell (order of the atomics)
   int* members;         // [n] particles grouped by cell, any order within a cell
@@ -347,14 +351,15 @@ __device__ __forceinline__ float hi_df(double x) {
   return h;
 }
 
-// Writes the FP32 shadow and render of a particle from its split position (h, l),
-// velocities and radius.
-__device__ __forceinline__ void write_render(float4* sh, float4* rd, const float* h, const float* l, const double* v,
-                                            const double* w, float R, bool active) {
-  sh[0] = make_float4(h[0], h[1], h[2], R);
-  rd[0] = make_float4(l[0], l[1], l[2], active ? 1.0f : 0.0f);
-  rd[1] = make_float4(d2f_int(v[0]), d2f_int(v[1]), d2f_int(v[2]), d2f_int(w[0]));
-  rd[2] = make_float4(d2f_int(w[1]), d2f_int(w[2]), 0.0f, 0.0f);
+// Writes the FP32 copy of a particle (render) from its split position (h, l) and its
+// velocities.  A particle out of the system is put at kFar on every axis: its distance
+// to any particle in the domain exceeds every contact and list reach, so no pair with it
+// touches or enters an inner list.
+__device__ __forceinline__ void write_render(float4* rd, const float* h, const float* l, const double* v,
+                                            const double* w, bool active) {
+  rd[0] = active ? make_float4(h[0], h[1], h[2], l[0]) : make_float4(kFar, kFar, kFar, 0.0f);
+  rd[1] = make_float4(l[1], l[2], d2f_int(v[0]), d2f_int(v[1]));
+  rd[2] = make_float4(d2f_int(v[2]), d2f_int(w[0]), d2f_int(w[1]), d2f_int(w[2]));
 }
 
 // b - a as an unevaluated FP32 pair (s, t), exact up to the rounding of the low parts.
@@ -362,6 +367,24 @@ __device__ __forceinline__ void df_diff(float ah, float al, float bh, float bl, 
   float e;
   two_sum(bh, -ah, s, e);
   t = __fadd_rn(__fsub_rn(bl, al), e);
+}
+
+// Upper bound on how far a particle has moved since the last inner-list refresh: its new
+// position hn + ln against the hi parts of the refresh position (the lo parts are not
+// kept; split_df truncates, so each was below 2^-23 of its coordinate, and together they
+// add at most sqrt(3) 2^-23 max|x_in| to the distance).  The factor 1 + 1e-5 covers the
+// FP32 rounding of the sum and the root.
+__device__ __forceinline__ float moved_since_inner(const float* xin, int n, int i, const float* hn, const float* ln) {
+  float d2 = 0.f, a = 0.f;
+  for (int d = 0; d < 3; d++) {
+    const float r = xin[(size_t)d * n + i];
+    float s1, t1;
+    df_diff(r, 0.0f, hn[d], ln[d], s1, t1);
+    const float u = s1 + t1;
+    d2 += u * u;
+    a = fmaxf(a, fabsf(r));
+  }
+  return sqrtf(d2) * (1.0f + 1e-5f) + 1.7320509f * 1.1920929e-7f * 1.0001f * a;
 }
 
 // Monotone map of a double's bits to a signed integer (exact ordering, integer ops only).

@@ -220,11 +220,11 @@ __global__ void k_permute(Params P) {
       xr[d * n + q] = h[d];
       xr[(3 + d) * n + q] = l[d];
     }
-    write_render(P.shadow[nxt] + q, P.render[nxt] + 3 * (size_t)q, h, l, vv, wv, r, a != 0);
+    write_render(P.render[nxt] + 3 * (size_t)q, h, l, vv, wv, a != 0);
   } else {
     for (int d = 0; d < 3; d++) P.xref[d * n + q] = xv[d];
-    P.shadow[nxt][q] = make_float4(h[0], h[1], h[2], r);
   }
+  P.shadow[nxt][q] = make_float4(h[0], h[1], h[2], r);
   P.act[nxt][q] = a;
   P.rad[sb ^ 1][q] = r;
   P.id[sb ^ 1][q] = P.id[sb][p];
@@ -396,7 +396,6 @@ __global__ void k_hist_load(Params P) {
           H[hcomp(P.n, rank, 0)] = sg * P.hval[3 * (size_t)h];
           H[hcomp(P.n, rank, 1)] = sg * P.hval[3 * (size_t)h + 1];
           H[hcomp(P.n, rank, 2)] = sg * P.hval[3 * (size_t)h + 2];
-          H[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           m |= 1ull << k;
           rank++;
         } else {
@@ -415,7 +414,6 @@ __global__ void k_hist_load(Params P) {
       H[hcomp(P.n, rank, 0)] = src[0];
       H[hcomp(P.n, rank, 1)] = src[1];
       H[hcomp(P.n, rank, 2)] = src[2];
-      H[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
       m |= 1ull << (kMaxNbr + w);
       rank++;
     } else {
@@ -444,9 +442,10 @@ __global__ void k_inner_build(Params P) {
     return;
   }
   const int cur = C->cur;
-  const float4* SH = P.shadow[cur];
-  const float4 hi = SH[q];
-  const float4 lo4 = P.render[cur][3 * (size_t)q];
+  const float4* RD = P.render[cur];
+  const float* RAD = P.rad[C->sbuf];
+  const float4 q0 = RD[3 * (size_t)q], q1 = RD[3 * (size_t)q + 1];
+  const float4 hi = make_float4(q0.x, q0.y, q0.z, RAD[q]);
   const float ai = max_abs3(hi);
   const int* nb = P.nbr + (size_t)q * kMaxNbr;
   const int cnt = P.nbr_cnt[q];
@@ -457,9 +456,10 @@ __global__ void k_inner_build(Params P) {
   bool overflow = false;
   for (int k = 0; k < cnt; k++) {
     const int j = nb[k];
-    const float4 hj = SH[j];
+    const float4 hj = RD[3 * (size_t)j];   // x_hi
+    if (hj.x == kFar) continue;             // out of the system: never a contact
     const float ex = hj.x - hi.x, ey = hj.y - hi.y, ez = hj.z - hi.z;
-    const float reach = hi.w + hj.w + P.f_inner_margin;
+    const float reach = hi.w + RAD[j] + P.f_inner_margin;
     const float up = reach + hi_distance_error(ai, max_abs3(hj), 2.0f * reach);
     if (ex * ex + ey * ey + ez * ez > up * up * (1.0f + 1e-6f)) continue;
     if (m < kInnerMax) {
@@ -475,7 +475,7 @@ __global__ void k_inner_build(Params P) {
   if (P.pair_once) P.inner_lo[q] = (uint8_t)mlo;
   if (overflow) atomicOr(&C->status, kStCapacity);
   const float* xr = reinterpret_cast<const float*>(P.xref);
-  const float h[3] = {hi.x, hi.y, hi.z}, l[3] = {lo4.x, lo4.y, lo4.z};
+  const float h[3] = {hi.x, hi.y, hi.z}, l[3] = {q0.w, q1.x, q1.y};
   float d2 = 0.0f;
   for (int d = 0; d < 3; d++) {
     float s1, t1;
@@ -483,9 +483,8 @@ __global__ void k_inner_build(Params P) {
     const float u = s1 + t1;
     d2 += u * u;
     P.xin[d * n + q] = h[d];
-    P.xin[(3 + d) * n + q] = l[d];
   }
-  P.xin[6 * n + q] = sqrtf(d2) * (1.0f + 1e-5f);
+  P.xin[3 * n + q] = sqrtf(d2) * (1.0f + 1e-5f);
 }
 
 // One evaluation per pair: for every slot of a particle's inner list whose pair it owns

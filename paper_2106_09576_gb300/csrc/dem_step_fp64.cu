@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
           Hnew[hcomp(P.n, rank, 0)] = H[0];
           Hnew[hcomp(P.n, rank, 1)] = H[1];
           Hnew[hcomp(P.n, rank, 2)] = H[2];
-          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << k;
           rank++;
         } else {
@@ -174,7 +173,6 @@ __global__ void __launch_bounds__(kStepBlock) k_step_fp64(const __grid_constant_
           Hnew[hcomp(P.n, rank, 0)] = H[0];
           Hnew[hcomp(P.n, rank, 1)] = H[1];
           Hnew[hcomp(P.n, rank, 2)] = H[2];
-          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << bit;
           rank++;
         } else {

@@ -6,10 +6,11 @@
 // delta / 2).
 // FP64 instructions issue at 1/72 of the FP32 rate on this part, so the kernel keeps them
 // to the integration (9 FMAs per particle) and the tangential-overlap accumulation
-// (3 adds per contact).  Every particle publishes, once per step, FP32 copies of itself
-// for its neighbours: a 16-byte shadow {x_hi, R} that the list builds read, and a
-// 48-byte render {x_lo, in-system flag, v, w} that a contact partner reads; its own
-// thread starts from them too and reads its FP64 state only for walls and integration.
+// (3 adds per contact).  Every particle publishes, once per step, a 48-byte FP32 copy of
+// itself for its neighbours, {x_hi, x_lo, v, w} (the radius is in its own array, and a
+// particle out of the system sits at kFar); the inner-list build and a contact partner
+// read it, its own thread starts from it too and reads its FP64 state only for walls and
+// integration.
 //   - relative positions are exact two-sum differences of the hi + lo pairs, so nearly
 //     co-located spheres keep their relative position to ~1e-7;
 //   - the normal overlap is (S^2 - r^2) / (S + r) with S^2 - r^2 formed exactly as a
@@ -110,9 +111,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
   const double* X = P.x[cur];
   const double* V = P.v[cur];
   const double* W = P.w[cur];
-  const float4* SH = P.shadow[cur];
   const float4* RD = P.render[cur];
-  float4* SHo = P.shadow[nxt];
+  const float* RAD = P.rad[C->sbuf];
   float4* RDo = P.render[nxt];
 
   if (last && i >= nact && i < n) {
@@ -124,9 +124,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
     }
   }
   if (i < nact) {
-    const float4 o0 = SH[i];
-    const float4 o1 = RD[3 * (size_t)i];
-    if (o1.w == 0.0f) {
+    const float4 o0 = RD[3 * (size_t)i];
+    if (o0.x == kFar) {
       for (int d = 0; d < 3; d++) {
         const double xv = X[d * n + i], vv = V[d * n + i], wv = W[d * n + i];
         P.x[nxt][d * n + i] = xv;
@@ -141,11 +140,11 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       }
       P.act[nxt][i] = 0;
       P.mask[hc ^ 1][i] = 0ull;
-      SHo[i] = o0;
       for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
     } else {
-      const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o1.x, o1.y, o1.z};
-      const float Rif = o0.w;
+      const float4 o1 = RD[3 * (size_t)i + 1];
+      const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o0.w, o1.x, o1.y};
+      const float Rif = RAD[i];
       // materials and walls: the context's, or those of the particle's instance in a batch
       const InstDev* I = kBatch ? P.itab + P.inst[C->sbuf][i] : nullptr;
       const MatF& Mt = kBatch ? I->mf : P.mf;
@@ -156,8 +155,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       const uint8_t* irow = P.inner + (size_t)i * kInnerMax;
       const int* jrow = P.inner_j + (size_t)i * kInnerMax;
       const int icnt = P.inner_cnt[i];
-      const float4 o2 = RD[3 * (size_t)i + 1], o3 = RD[3 * (size_t)i + 2];
-      const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
+      const float4 o2 = RD[3 * (size_t)i + 2];
+      const float vif[3] = {o1.z, o1.w, o2.x}, wif[3] = {o2.y, o2.z, o2.w};
       const unsigned long long mold = P.mask[hc][i];
       const double* Hold = P.hist[hc] + (size_t)i;
       double* Hnew = P.hist[hc ^ 1] + (size_t)i;
@@ -171,9 +170,9 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       for (int slot = 0; slot < icnt; slot++) {
         const int k = irow[slot];
         const int j = jrow[slot];
-        const float4 r0 = SH[j];
         const float4* rj = RD + 3 * (size_t)j;
-        const float4 r1 = rj[0], r2 = rj[1], r3 = rj[2];
+        const float4 r0 = rj[0], r1 = rj[1], r2 = rj[2];
+        const float Rjf = RAD[j];
         double H[3] = {0.0, 0.0, 0.0};
         if ((mold >> k) & 1ull) {
           const int ro = __popcll(mold & ((1ull << k) - 1ull));
@@ -181,12 +180,11 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
           H[1] = Hold[hcomp(P.n, ro, 1)];
           H[2] = Hold[hcomp(P.n, ro, 2)];
         }
-        if (r1.w == 0.0f) continue;                    // partner out of the system
-        const float Rjf = r0.w;
+        if (r0.x == kFar) continue;                    // partner out of the system
         float s[3], t[3], dxf[3];
-        df_diff(hx[0], lx[0], r0.x, r1.x, s[0], t[0]);
-        df_diff(hx[1], lx[1], r0.y, r1.y, s[1], t[1]);
-        df_diff(hx[2], lx[2], r0.z, r1.z, s[2], t[2]);
+        df_diff(hx[0], lx[0], r0.x, r0.w, s[0], t[0]);
+        df_diff(hx[1], lx[1], r0.y, r1.x, s[1], t[1]);
+        df_diff(hx[2], lx[2], r0.z, r1.y, s[2], t[2]);
         for (int d = 0; d < 3; d++) dxf[d] = s[d] + t[d];
         const float S = Rif + Rjf;
         // S^2 - r^2 as an exact double-float
@@ -210,8 +208,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         const float dn = D / (Sh + r);                   // Eq. deltan without cancellation
         const float ir = 1.0f / r;
         const float nrm[3] = {dxf[0] * ir, dxf[1] * ir, dxf[2] * ir};   // Eq. vecn
-        const float wj[3] = {r2.w, r3.x, r3.y};
-        const float dv[3] = {vif[0] - r2.x, vif[1] - r2.y, vif[2] - r2.z};
+        const float wj[3] = {r2.y, r2.z, r2.w};
+        const float dv[3] = {vif[0] - r1.z, vif[1] - r1.w, vif[2] - r2.x};
         const float dw[3] = {wif[0] - wj[0], wif[1] - wj[1], wif[2] - wj[2]};
         // R_i w_i + R_j w_j rounded identically on both sides of the pair (no contraction),
         // so the two sides' tangential overlaps stay exact opposites and a contact search,
@@ -234,7 +232,6 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
           Hnew[hcomp(P.n, rank, 0)] = H[0];
           Hnew[hcomp(P.n, rank, 1)] = H[1];
           Hnew[hcomp(P.n, rank, 2)] = H[2];
-          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << k;
           rank++;
         } else {
@@ -278,7 +275,6 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
           Hnew[hcomp(P.n, rank, 0)] = o.H[0];
           Hnew[hcomp(P.n, rank, 1)] = o.H[1];
           Hnew[hcomp(P.n, rank, 2)] = o.H[2];
-          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << (kMaxNbr + k);
           rank++;
         } else {
@@ -320,7 +316,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       P.act[nxt][i] = alive ? 1 : 0;
       float hn[3], ln[3];
       for (int d = 0; d < 3; d++) split_df(xn[d], hn[d], ln[d]);
-      write_render(SHo + i, RDo + 3 * (size_t)i, hn, ln, vn, wn, Rif, alive);
+      write_render(RDo + 3 * (size_t)i, hn, ln, vn, wn, alive);
       if (!(finite_d(xn[0]) && finite_d(xn[1]) && finite_d(xn[2]) && finite_d(vn[0]) && finite_d(vn[1]) &&
             finite_d(vn[2])))
         st.status |= kStNonfinite;
@@ -330,16 +326,9 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         // |x^{n+1} - x_in| > delta / 2; the contact search (as the method states it) when
         // |x^{n+1} - x_ref| > skin / 2, which is tested only when |x^{n+1} - x_in| plus the
         // stored |x_in - x_ref| come near skin / 2 (below, it cannot hold)
-        const float* xr = P.xin;
-        float d2 = 0.f;
-        for (int d = 0; d < 3; d++) {
-          float s1, t1;
-          df_diff(xr[d * n + i], xr[(3 + d) * n + i], hn[d], ln[d], s1, t1);
-          const float u = s1 + t1;
-          d2 += u * u;
-        }
-        if (d2 > P.f_inner_lim2) P.ctl->need_inner = 1;
-        if (P.rebuild_every <= 0 && sqrtf(d2) * (1.0f + 1e-5f) + xr[6 * n + i] > P.f_disp_lim * (1.0f - 1e-5f)) {
+        const float dm = moved_since_inner(P.xin, n, i, hn, ln);
+        if (dm * dm > P.f_inner_lim2) P.ctl->need_inner = 1;
+        if (P.rebuild_every <= 0 && dm + P.xin[3 * (size_t)n + i] > P.f_disp_lim * (1.0f - 1e-5f)) {
           const float* xs = reinterpret_cast<const float*>(P.xref);
           float e2 = 0.f;
           for (int d = 0; d < 3; d++) {
@@ -390,8 +379,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
   StepStats st = {0u, 0u, 0u, 0.0f, 0u};
   const double* X = P.x[cur];
   // read-only in this kernel: the compiler may issue these loads ahead of the stores
-  const float4* __restrict__ SH = P.shadow[cur];
   const float4* __restrict__ RD = P.render[cur];
+  const float* __restrict__ RAD = P.rad[C->sbuf];
   if (i < nact) {
     const int icnt = P.inner_cnt[i], ilo = P.inner_lo[i];
     const int nown = icnt - ilo;
@@ -399,11 +388,10 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
     // the first owned slot is fetched with the own data, each next one during the
     // current pair's arithmetic
     int2 e = nown > 0 ? __ldg(ps) : make_int2(0, 0);
-    const float4 o0 = __ldg(SH + i);
-    const float4 o1 = __ldg(RD + 3 * (size_t)i);
+    const float4 o0 = __ldg(RD + 3 * (size_t)i);
     const float zero[3] = {0.f, 0.f, 0.f};
     float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
-    if (o1.w == 0.0f) {
+    if (o0.x == kFar) {
       // out of the system: its pairs exert nothing, and its partners' records say so
       for (int t = 0; t < nown; t++) {
         const int2 f = __ldg(ps + (size_t)t * n);
@@ -412,12 +400,12 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
       }
       P.mask[hc ^ 1][i] = 0ull;
     } else {
-      const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o1.x, o1.y, o1.z};
-      const float Rif = o0.w;
+      const float4 o1 = __ldg(RD + 3 * (size_t)i + 1), o2 = __ldg(RD + 3 * (size_t)i + 2);
+      const float hx[3] = {o0.x, o0.y, o0.z}, lx[3] = {o0.w, o1.x, o1.y};
+      const float Rif = __ldg(RAD + i);
       const InstDev* I = kBatch ? P.itab + P.inst[C->sbuf][i] : nullptr;
       const MatF& Mt = kBatch ? I->mf : P.mf;
-      const float4 o2 = __ldg(RD + 3 * (size_t)i + 1), o3 = __ldg(RD + 3 * (size_t)i + 2);
-      const float vif[3] = {o2.x, o2.y, o2.z}, wif[3] = {o2.w, o3.x, o3.y};
+      const float vif[3] = {o1.z, o1.w, o2.x}, wif[3] = {o2.y, o2.z, o2.w};
       const unsigned long long mold = __ldg(P.mask[hc] + i);
       const double* __restrict__ Hold = P.hist[hc] + (size_t)i;
       double* Hnew = P.hist[hc ^ 1] + (size_t)i;
@@ -429,9 +417,9 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
         const int j = e.x;
         const int k = e.y & 0xFF;
         const int m = (e.y >> 8) & 0xFF;
-        const float4 r0 = __ldg(SH + j);
         const float4* rj = RD + 3 * (size_t)j;
-        const float4 r1 = __ldg(rj), r2 = __ldg(rj + 1), r3 = __ldg(rj + 2);
+        const float4 r0 = __ldg(rj), r1 = __ldg(rj + 1), r2 = __ldg(rj + 2);
+        const float rj_R = __ldg(RAD + j);
         double H[3] = {0.0, 0.0, 0.0};
         if ((mold >> k) & 1ull) {
           const int ro = __popcll(mold & ((1ull << k) - 1ull));
@@ -444,11 +432,11 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
         bool touch = false;
         float Rjf = 0.f, D = 0.f, Sh = 0.f, Ah = 0.f, Al = 0.f;
         float s3[3], t3[3];
-        if (r1.w != 0.0f) {                              // partner in the system
-          Rjf = r0.w;
-          df_diff(hx[0], lx[0], r0.x, r1.x, s3[0], t3[0]);
-          df_diff(hx[1], lx[1], r0.y, r1.y, s3[1], t3[1]);
-          df_diff(hx[2], lx[2], r0.z, r1.z, s3[2], t3[2]);
+        if (r0.x != kFar) {                              // partner in the system
+          Rjf = rj_R;
+          df_diff(hx[0], lx[0], r0.x, r0.w, s3[0], t3[0]);
+          df_diff(hx[1], lx[1], r0.y, r1.x, s3[1], t3[1]);
+          df_diff(hx[2], lx[2], r0.z, r1.y, s3[2], t3[2]);
           // S^2 - r^2 as an exact double-float
           float p2, pe, e2;
           two_prod(s3[0], s3[0], Ah, pe);
@@ -475,8 +463,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
           const float dn = D / (Sh + r);                   // Eq. deltan without cancellation
           const float ir = 1.0f / r;
           const float nrm[3] = {dxf[0] * ir, dxf[1] * ir, dxf[2] * ir};   // Eq. vecn
-          const float wj[3] = {r2.w, r3.x, r3.y};
-          const float dv[3] = {vif[0] - r2.x, vif[1] - r2.y, vif[2] - r2.z};
+          const float wj[3] = {r2.y, r2.z, r2.w};
+          const float dv[3] = {vif[0] - r1.z, vif[1] - r1.w, vif[2] - r2.x};
           const float dw[3] = {wif[0] - wj[0], wif[1] - wj[1], wif[2] - wj[2]};
           float rw[3];
           for (int d = 0; d < 3; d++) rw[d] = __fadd_rn(__fmul_rn(Rif, wif[d]), __fmul_rn(Rjf, wj[d]));
@@ -546,7 +534,6 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
           Hnew[hcomp(P.n, rank, 0)] = o.H[0];
           Hnew[hcomp(P.n, rank, 1)] = o.H[1];
           Hnew[hcomp(P.n, rank, 2)] = o.H[2];
-          Hnew[hcomp(P.n, rank, 3)] = 0.0;   // the pad: the entry's sector is written whole
           mnew |= 1ull << (kMaxNbr + k);
           rank++;
         } else {
@@ -568,7 +555,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
 constexpr int kIntBlock = 256;
 
 template <bool kExt>
-__global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__ Params P) {
+__global__ void __launch_bounds__(kIntBlock, 4) k_int_mixed(const __grid_constant__ Params P) {
   const Control* C = P.ctl;
   const int cur = C->cur, nxt = cur ^ 1, hc = C->hc;
   const bool init = C->init != 0, last = C->last != 0;
@@ -578,9 +565,7 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
   const double* X = P.x[cur];
   const double* V = P.v[cur];
   const double* W = P.w[cur];
-  const float4* SH = P.shadow[cur];
   const float4* RD = P.render[cur];
-  float4* SHo = P.shadow[nxt];
   float4* RDo = P.render[nxt];
 
   if (last && i >= nact && i < n) {
@@ -592,10 +577,9 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
     }
   }
   if (i < nact) {
-    // the in-system flag and the radius from their own arrays (the FP32 copies hold the
-    // same values): 5 bytes instead of two 16-byte vectors
+    // the in-system flag and the radius from their own arrays: 5 bytes instead of the
+    // FP32 copy's first vector
     if (P.act[cur][i] == 0) {
-      const float4 o0 = SH[i];
       for (int d = 0; d < 3; d++) {
         const double xv = X[d * n + i], vv = V[d * n + i], wv = W[d * n + i];
         P.x[nxt][d * n + i] = xv;
@@ -609,7 +593,6 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
         }
       }
       P.act[nxt][i] = 0;
-      SHo[i] = o0;
       for (int k = 0; k < 3; k++) RDo[3 * (size_t)i + k] = RD[3 * (size_t)i + k];
     } else {
       // every independent load first: the FP64 state and the owner sums do not depend on
@@ -676,22 +659,15 @@ __global__ void __launch_bounds__(kIntBlock) k_int_mixed(const __grid_constant__
       P.act[nxt][i] = alive ? 1 : 0;
       float hn[3], ln[3];
       for (int d = 0; d < 3; d++) split_df(xn[d], hn[d], ln[d]);
-      write_render(SHo + i, RDo + 3 * (size_t)i, hn, ln, vn, wn, Rif, alive);
+      write_render(RDo + 3 * (size_t)i, hn, ln, vn, wn, alive);
       if (!(finite_d(xn[0]) && finite_d(xn[1]) && finite_d(xn[2]) && finite_d(vn[0]) && finite_d(vn[1]) &&
             finite_d(vn[2])))
         st.status |= kStNonfinite;
       if (alive) {
         st.active++;
-        const float* xr = P.xin;
-        float d2 = 0.f;
-        for (int d = 0; d < 3; d++) {
-          float s1, t1;
-          df_diff(xr[d * n + i], xr[(3 + d) * n + i], hn[d], ln[d], s1, t1);
-          const float u = s1 + t1;
-          d2 += u * u;
-        }
-        if (d2 > P.f_inner_lim2) P.ctl->need_inner = 1;
-        if (P.rebuild_every <= 0 && sqrtf(d2) * (1.0f + 1e-5f) + xr[6 * n + i] > P.f_disp_lim * (1.0f - 1e-5f)) {
+        const float dm = moved_since_inner(P.xin, n, i, hn, ln);
+        if (dm * dm > P.f_inner_lim2) P.ctl->need_inner = 1;
+        if (P.rebuild_every <= 0 && dm + P.xin[3 * (size_t)n + i] > P.f_disp_lim * (1.0f - 1e-5f)) {
           const float* xs = reinterpret_cast<const float*>(P.xref);
           float e2 = 0.f;
           for (int d = 0; d < 3; d++) {

@@ -1,12 +1,13 @@
 // surrogate.cu -- the learned surrogate of the DEM drum (include/surrogate.h): a
 // message-passing network on the contact graph, trained and run with BF16 tensor-core
-// products (mma.sync m16n8k16, FP32 accumulation) and deterministic segment sums.
+// products (tcgen05 for the 128-wide products of the forward pass and the data gradients,
+// mma.sync m16n8k16 for the rest; FP32 accumulation) and deterministic segment sums.
 //
-// Every product of the network goes through one tiled GEMM kernel whose A operand is read
-// through an accessor: the concatenation [S0[g(r)] | S1[r]] of two BF16 row blocks (g an
-// optional row gather), either as A or transposed (for weight gradients, where the long
-// dimension -- edges or nodes -- is the reduction, split over blocks with FP32 partial sums
-// reduced in a fixed order).  Aggregations over the receiver-sorted CSR are segment sums, so
+// The other products -- the weight gradients, where the long dimension (edges or nodes) is
+// the reduction, and the decoder's 8-wide ones -- go through one tiled mma.sync GEMM kernel
+// whose A operand is read through an accessor: the concatenation [S0[g(r)] | S1[r]] of two
+// BF16 row blocks (g an optional row gather), either as A or transposed (weight gradients,
+// split over blocks with FP32 partial sums reduced in a fixed order).  Aggregations over the receiver-sorted CSR are segment sums, so
 // forward and backward results do not depend on thread timing (no float atomics).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -268,6 +269,15 @@ __global__ void k_relu_back(const float* dout, int64_t ld_dout, const bf16* u, i
 }
 
 // dst[m][n] += src[m * lds + n] for the first N columns (FP32)
+// Block c0 of W^T for a data gradient: Wt[c][j] = W[c0 + j][c], W row-major [K][H] (rows
+// c0 .. c0 + H - 1 used), so that dz Wt is columns c0 .. c0 + H - 1 of dz W^T.
+__global__ void k_wt_block(const bf16* W, int c0, bf16* Wt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= H * H) return;
+  const int c = t / H, j = t % H;
+  Wt[t] = W[(int64_t)(c0 + j) * H + c];
+}
+
 __global__ void k_add_cols(float* dst, const float* src, int64_t lds, int64_t M, int N) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= M * N) return;
@@ -416,6 +426,7 @@ struct WS {
   float *dh;     // [n][H]
   float *dh2;    // [n][H]
   float *part;   // [kSplit][2H][H]
+  bf16 *wt;      // [7][H][H] transposed weight blocks of the data gradients (layers 4, 3, 2: two each; 1: one)
   int32_t* recv; // [nE]
   float* mse;    // [1024]
   size_t total;
@@ -451,6 +462,7 @@ WS layout_ws(char* base, int64_t n, int64_t nE) {
   w.dh = (float*)take(n * H * 4);
   w.dh2 = (float*)take(n * H * 4);
   w.part = (float*)take((size_t)kSplit * 2 * H * H * 4);
+  w.wt = (bf16*)take((size_t)7 * H * H * 2);
   w.recv = (int32_t*)take(nE * 4);
   w.mse = (float*)take(1024 * 4);
   w.total = o;
@@ -647,6 +659,21 @@ extern "C" int surr_backward(const void* params_bf16, const float* dY, const int
   gemm_wgrad(CatA{w.h3, nullptr, H, nullptr, 0}, MatB{w.dzb, NOUT, 0}, H, NOUT, n, w.part, grad + L.W[5], s);
   k_colsum<<<NOUT, 256, 0, s>>>(w.dzf, n, NOUT, grad + L.b[5]);
   gemm(CatA{w.dzb, nullptr, NOUT, nullptr, 0}, MatB{Pb + L.W[5], NOUT, 1}, n, H, NOUT, w.dh, s);
+  // The data gradients dz W^T of the 128-wide layers run on the tensor cores (the forward
+  // pass's tcgen05 product, no bias and no activation, FP32 out), one 128-column block of
+  // W^T at a time: blocks of layers 4, 3, 2 (two each) and 1 (the h0[recv] rows only: the
+  // edge features need no gradient).
+  const int wt_layer[7] = {4, 4, 3, 3, 2, 2, 1};
+  for (int b = 0; b < 7; b++)
+    k_wt_block<<<nblk(H * H, T), T, 0, s>>>(Pb + L.W[wt_layer[b]], (b & 1) ? H : 0, w.wt + (size_t)b * H * H);
+  auto dgrad = [&](int b, int64_t M, float* out) {
+    surrtc::Args a{w.dzb, nullptr, H, nullptr, 0, w.wt + (size_t)b * H * H, nullptr, 0, nullptr, nullptr, nullptr,
+                   out, M};
+    return surrtc::launch(a, s);
+  };
+  bool ok = true;
+  float* C0 = w.C;                  // [M][H]: columns 0 .. H - 1 of dz W^T
+  float* C1 = w.C + (size_t)n * H;  // [n][H]: columns H .. 2H - 1
   // ---- node layers: h_out = h_in + u, u = relu([h_in | s] W + b), s = neighbour sum of h_in
   const bf16* hin[2] = {w.h1, w.h2};
   const bf16* sin[2] = {w.s1, w.s2};
@@ -658,26 +685,26 @@ extern "C" int surr_backward(const void* params_bf16, const float* dY, const int
     k_colsum<<<H, 256, 0, s>>>(w.dzf, n, H, grad + L.b[l]);
     // d[h_in | s] = dz W^T; dh_in = dh_out + d[:, :H] + (neighbour sum of d[:, H:]) -- the
     // graph is symmetric, so the transpose of the neighbour sum is the neighbour sum
-    gemm(CatA{w.dzb, nullptr, H, nullptr, 0}, MatB{Pb + L.W[l], H, 1}, n, 2 * H, H, w.C, s);
-    k_add_cols<<<nblk(n * H, T), T, 0, s>>>(w.dh, w.C, 2 * H, n, H);
-    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, nullptr, w.C + H, 2 * H, n, nullptr, w.dh, 1, kAgg);
+    ok = ok && dgrad(2 * (4 - l), n, C0) && dgrad(2 * (4 - l) + 1, n, C1);
+    k_add_cols<<<nblk(n * H, T), T, 0, s>>>(w.dh, C0, H, n, H);
+    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, col, nullptr, C1, H, n, nullptr, w.dh, 1, kAgg);
   }
   // ---- layer 2: h1 = h0 + u2, u2 = relu([h0 | a] W2 + b2), a = sum of the edge messages
   k_relu_back<<<nblk(n * H, T), T, 0, s>>>(w.dh, H, w.u2, n, H, 1, w.dzb, w.dzf);
   gemm_wgrad(CatA{w.h0, nullptr, H, w.a, H}, MatB{w.dzb, H, 0}, 2 * H, H, n, w.part, grad + L.W[2], s);
   k_colsum<<<H, 256, 0, s>>>(w.dzf, n, H, grad + L.b[2]);
-  gemm(CatA{w.dzb, nullptr, H, nullptr, 0}, MatB{Pb + L.W[2], H, 1}, n, 2 * H, H, w.C, s);
-  k_add_cols<<<nblk(n * H, T), T, 0, s>>>(w.dh, w.C, 2 * H, n, H);           // dh0 (so far)
+  ok = ok && dgrad(4, n, C0) && dgrad(5, n, C1);
+  k_add_cols<<<nblk(n * H, T), T, 0, s>>>(w.dh, C0, H, n, H);                // dh0 (so far)
   // da = d[:, H:] (dense FP32 copy)
-  k_relu_back<<<nblk(n * H, T), T, 0, s>>>(w.C + H, 2 * H, nullptr, n, H, 0, w.dzb, w.dh2);
+  k_relu_back<<<nblk(n * H, T), T, 0, s>>>(C1, H, nullptr, n, H, 0, w.dzb, w.dh2);
   // ---- layer 1 (edges): u1 = relu([h0[recv] | E] W1 + b1)
   if (nE > 0) {
     k_gather_mask<<<nblk(nE * H, T), T, 0, s>>>(w.dh2, w.recv, w.u1, nE, w.dzb, w.dzf);
     gemm_wgrad(CatA{w.h0, w.recv, H, w.Eb, EIN}, MatB{w.dzb, H, 0}, H + EIN, H, nE, w.part, grad + L.W[1], s);
     k_colsum<<<H, 256, 0, s>>>(w.dzf, nE, H, grad + L.b[1]);
-    gemm(CatA{w.dzb, nullptr, H, nullptr, 0}, MatB{Pb + L.W[1], H, 1}, nE, H + EIN, H, w.C, s);
+    ok = ok && dgrad(6, nE, C0);
     // dh0[i] += sum over the edges into i of d[e, :H]
-    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, nullptr, nullptr, w.C, H + EIN, n, nullptr, w.dh, 1, 1.0f);
+    k_segsum<<<nblk(n * 32, T), T, 0, s>>>(row_ptr, nullptr, nullptr, C0, H, n, nullptr, w.dh, 1, 1.0f);
   } else {
     cudaMemsetAsync(grad + L.W[1], 0, (size_t)(L.b[1] - L.W[1] + H) * 4, s);
   }
@@ -685,6 +712,7 @@ extern "C" int surr_backward(const void* params_bf16, const float* dY, const int
   k_relu_back<<<nblk(n * H, T), T, 0, s>>>(w.dh, H, w.h0, n, H, 1, w.dzb, w.dzf);
   gemm_wgrad(CatA{w.Xb, nullptr, FIN, nullptr, 0}, MatB{w.dzb, H, 0}, FIN, H, n, w.part, grad + L.W[0], s);
   k_colsum<<<H, 256, 0, s>>>(w.dzf, n, H, grad + L.b[0]);
+  if (!ok) return 2;
   return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

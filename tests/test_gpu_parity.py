@@ -282,6 +282,81 @@ def test_capacity_error_is_reported():
         g.step(1)                        # sticky until the state is set again
 
 
+def crowded_sphere(k, seed=81):
+    """One sphere of radius 5 mm with k spheres of radius 1 mm on its surface (Fibonacci
+    directions, each overlapping it by 2 % of the small radius; at k <= 33 the small spheres
+    are more than 3 mm apart, so none touches another): the big sphere holds k contacts at
+    once.  Random velocities and spins give every pair a tangential overlap."""
+    Rb, r = 5e-3, 1e-3
+    c = np.array([0.05, 0.05, 0.05])
+    t = np.arange(k) + 0.5
+    phi = np.arccos(1.0 - 2.0 * t / k)
+    th = np.pi * (1.0 + 5.0 ** 0.5) * t
+    u = np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1)
+    x = np.vstack([c, c + (Rb + r - 0.02 * r) * u])
+    R = np.array([Rb] + [r] * k, dtype=np.float32)
+    rng = np.random.default_rng(seed)
+    v = rng.normal(0.0, 0.02, (k + 1, 3))
+    w = rng.normal(0.0, 2.0, (k + 1, 3))
+    cfg = dict(density=2500.0, particle=workloads.material(), wall=workloads.material(),
+               gravity=(0, 0, 0), dt=1e-6, neighbor_factor=1.3, domain_lo=(0, 0, 0),
+               domain_hi=(0.1, 0.1, 0.1))
+    return workloads.Workload("crowded", cfg, [], x, v, w, R)
+
+
+def test_sphere_holding_every_contact_slot():
+    # 32 simultaneous contacts: every slot of the compact overlap list (and, in the mixed
+    # path, of the inner list) is in use.  FP64: bit-exact with the oracle over 50 steps.
+    # Mixed, both pair evaluations: forces and torques of the first evaluation (tangential
+    # overlaps on every pair) within tolerance, positions after 50 steps close, no capacity
+    # error.  Later torques are not compared: at these sizes the constant rolling
+    # resistance stops a small sphere's relative spin within a few steps (its torque turns
+    # the spin by ~0.4 rad/s per step), after which the torque's direction follows the
+    # sign of a vanishing relative spin in either precision.
+    wl = crowded_sphere(32)
+    d = wl.x[1:] - wl.x[1:, None]
+    assert np.sqrt((d ** 2).sum(-1) + np.eye(32)).min() > 3e-3
+    g, o = make_gpu(wl, "fp64"), make_oracle(wl)
+    g.step(50)
+    o.step(50)
+    compare_exact(g, o)
+    assert o.stats()["n_touch"] == 32
+    for pair_eval in ("once", "both"):
+        wm = crowded_sphere(32)
+        wm.cfg["pair_eval"] = pair_eval
+        gm, om = make_gpu(wm, "mixed"), make_oracle(wm)
+        tp = touching_pairs(wm.x, wm.radius.astype(np.float64))
+        assert len(tp) == 32
+        p, vals = random_history(wm, tp, 7, frac=1.0)
+        gm.set_history(p, vals)
+        om.set_history(p, vals)
+        Fg, Mg = gm.forces()
+        Fo, Mo = om.forces()
+        Fa, Ma = om.force_scales()
+        m = masses(wm)
+        ef = force_error(Fg, Fo, Fa, m, wm.cfg["gravity"])
+        em = torque_error(Mg, Mo, Ma, m, wm.radius.astype(float), wm.cfg["gravity"])
+        print(f"32 contacts, mixed ({pair_eval}), first evaluation: force {ef:.3e} torque {em:.3e}")
+        assert ef <= MIXED_TOL and em <= MIXED_TOL
+        gm.step(50)
+        om.step(50)
+        dx = np.abs(gm.state()[0] - om.state()[0]).max()
+        print(f"32 contacts, mixed ({pair_eval}), after 50 steps: max position difference {dx:.3e} m")
+        assert dx < 1e-7                    # a lost contact would move a sphere by ~5e-6 m
+        assert gm.stats()["n_touch"] == 32
+        gm.sync()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_one_contact_more_than_the_slots_is_a_capacity_error(precision):
+    from paper_2106_09576_gb300 import DemError
+    g = make_gpu(crowded_sphere(33), precision)
+    g.step(1)
+    with pytest.raises(DemError) as e:
+        g.sync()
+    assert e.value.code == 3
+
+
 def test_nonfinite_and_overlap_errors_are_reported():
     from paper_2106_09576_gb300 import DemError
     wl = dense(n=500, seed=71)
