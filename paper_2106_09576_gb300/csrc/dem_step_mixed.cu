@@ -21,6 +21,10 @@
 
 namespace demgb {
 
+// Sends the cache line of p towards L1 (no register holds the data): the step kernels
+// issue it for the next slot's partner while the current slot computes.
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // One particle-wall contact: FP64 geometry, FP32 law, FP64 overlap accumulation.  Few
 // particles touch a wall, so this is kept out of line: its FP64 temporaries would
 // otherwise set the register budget (and the spills) of the whole kernel.
@@ -179,6 +183,21 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
           H[0] = Hold[hcomp(P.n, ro, 0)];
           H[1] = Hold[hcomp(P.n, ro, 1)];
           H[2] = Hold[hcomp(P.n, ro, 2)];
+        }
+        // the next slot's partner copy, radius and overlap towards L1 (its row entries are
+        // in the sector just read)
+        if (slot + 1 < icnt) {
+          const int k1 = irow[slot + 1], j1 = jrow[slot + 1];
+          const char* r1p = reinterpret_cast<const char*>(RD + 3 * (size_t)j1);
+          prefetch_l1(r1p);
+          prefetch_l1(r1p + 32);
+          prefetch_l1(RAD + j1);
+          if ((mold >> k1) & 1ull) {
+            const int ro1 = __popcll(mold & ((1ull << k1) - 1ull));
+            prefetch_l1(Hold + hcomp(P.n, ro1, 0));
+            prefetch_l1(Hold + hcomp(P.n, ro1, 1));
+            prefetch_l1(Hold + hcomp(P.n, ro1, 2));
+          }
         }
         if (r0.x == kFar) continue;                    // partner out of the system
         float s[3], t[3], dxf[3];
@@ -388,6 +407,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
     // the first owned slot is fetched with the own data, each next one during the
     // current pair's arithmetic
     int2 e = nown > 0 ? __ldg(ps) : make_int2(0, 0);
+    int2 e1 = nown > 1 ? __ldg(ps + (size_t)n) : make_int2(0, 0);
     const float4 o0 = __ldg(RD + 3 * (size_t)i);
     const float zero[3] = {0.f, 0.f, 0.f};
     float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
@@ -427,7 +447,23 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
           H[1] = __ldg(Hold + hcomp(P.n, ro, 1));
           H[2] = __ldg(Hold + hcomp(P.n, ro, 2));
         }
-        if (t + 1 < nown) e = __ldg(ps + (size_t)(t + 1) * n);
+        // the next slot's partner copy, radius and overlap are sent towards L1 now, so that
+        // its loads hit there; the entry after it is fetched into a register
+        if (t + 1 < nown) {
+          const int j1 = e1.x, k1 = e1.y & 0xFF;
+          const char* r1p = reinterpret_cast<const char*>(RD + 3 * (size_t)j1);
+          prefetch_l1(r1p);
+          prefetch_l1(r1p + 32);
+          prefetch_l1(RAD + j1);
+          if ((mold >> k1) & 1ull) {
+            const int ro1 = __popcll(mold & ((1ull << k1) - 1ull));
+            prefetch_l1(Hold + hcomp(P.n, ro1, 0));
+            prefetch_l1(Hold + hcomp(P.n, ro1, 1));
+            prefetch_l1(Hold + hcomp(P.n, ro1, 2));
+          }
+          e = e1;
+          if (t + 2 < nown) e1 = __ldg(ps + (size_t)(t + 2) * n);
+        }
         float rf[3] = {0.f, 0.f, 0.f}, rm[3] = {0.f, 0.f, 0.f};
         bool touch = false;
         float Rjf = 0.f, D = 0.f, Sh = 0.f, Ah = 0.f, Al = 0.f;
