@@ -170,10 +170,13 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
       unsigned long long mnew = 0ull;
       int rank = 0;
 
-      // every load of a candidate is issued before any branch
+      // every load of a candidate is issued before any branch; the first row entry is read
+      // without waiting for the count (it exists for every particle; unused if the row is
+      // empty), each next one with the prefetch of its partner
+      int kc = irow[0], jc = jrow[0];
       for (int slot = 0; slot < icnt; slot++) {
-        const int k = irow[slot];
-        const int j = jrow[slot];
+        const int k = kc;
+        const int j = jc;
         const float4* rj = RD + 3 * (size_t)j;
         const float4 r0 = rj[0], r1 = rj[1], r2 = rj[2];
         const float Rjf = RAD[j];
@@ -188,6 +191,8 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         // in the sector just read)
         if (slot + 1 < icnt) {
           const int k1 = irow[slot + 1], j1 = jrow[slot + 1];
+          kc = k1;
+          jc = j1;
           const char* r1p = reinterpret_cast<const char*>(RD + 3 * (size_t)j1);
           prefetch_l1(r1p);
           prefetch_l1(r1p + 32);
@@ -404,10 +409,11 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
     const int icnt = P.inner_cnt[i], ilo = P.inner_lo[i];
     const int nown = icnt - ilo;
     const int2* __restrict__ ps = P.pslot + i;   // entry t at ps[t * n]: slot-major
-    // the first owned slot is fetched with the own data, each next one during the
-    // current pair's arithmetic
-    int2 e = nown > 0 ? __ldg(ps) : make_int2(0, 0);
-    int2 e1 = nown > 1 ? __ldg(ps + (size_t)n) : make_int2(0, 0);
+    // the first two owned-slot entries are read with the own data, without waiting for the
+    // counts (entries 0 and 1 exist for every particle; those beyond the owned count are
+    // never used); each later one during the arithmetic of the slot two before it
+    int2 e = __ldg(ps);
+    int2 e1 = __ldg(ps + (size_t)n);
     const float4 o0 = __ldg(RD + 3 * (size_t)i);
     const float zero[3] = {0.f, 0.f, 0.f};
     float Ff[3] = {0.f, 0.f, 0.f}, Mf[3] = {0.f, 0.f, 0.f};
