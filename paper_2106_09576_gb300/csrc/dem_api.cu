@@ -507,9 +507,16 @@ void fill_materials(const dem_material& part, const dem_material& wall, MatD* md
   mf->mur_pw = (float)md->mur_pw;
 }
 
-void to_device_wall(const dem_wall& s, WallDev* W, WallF* F, float* fv) {
+// A double as an FP32 pair h + l (h the nearest float, l the nearest float to the rest).
+void split_host(double v, float* h, float* l) {
+  *h = (float)v;
+  *l = (float)(v - (double)*h);
+}
+
+void to_device_wall(const dem_wall& s, WallDev* W, WallF* F, float* fv, WallX* X) {
   std::memset(W, 0, sizeof(*W));
   std::memset(F, 0, sizeof(*F));
+  std::memset(X, 0, sizeof(*X));
   W->kind = s.kind;
   W->translates = s.translates ? 1 : 0;
   double nn = std::sqrt(s.normal[0] * s.normal[0] + s.normal[1] * s.normal[1] + s.normal[2] * s.normal[2]);
@@ -532,15 +539,35 @@ void to_device_wall(const dem_wall& s, WallDev* W, WallF* F, float* fv) {
   F->radius = (float)W->radius;
   F->inner = (float)W->inner;
   for (int d = 0; d < 3; d++) fv[d] = W->translates ? (float)W->V[d] : 0.0f;
+  // the FP32 form: planes and cylinders along a coordinate axis that do not translate
+  X->axis = -1;
+  if ((W->kind == 0 || W->kind == 1) && !W->translates) {
+    for (int a = 0; a < 3; a++) {
+      const int b = (a + 1) % 3, c2 = (a + 2) % 3;
+      if (std::fabs(W->n[a]) == 1.0 && W->n[b] == 0.0 && W->n[c2] == 0.0) {
+        X->axis = a;
+        X->sign = (float)W->n[a];
+      }
+    }
+  }
+  for (int d = 0; d < 3; d++) {
+    split_host(W->p[d], &X->ph[d], &X->pl[d]);
+    X->Om[d] = (float)W->Om[d];
+    X->c[d] = (float)W->c[d];
+    X->V[d] = (float)W->V[d];
+  }
+  split_host(W->radius, &X->rh, &X->rl);
 }
 
 void fill_walls(dem_ctx* c) {
   for (int k = 0; k < kMaxWalls; k++) {
     if (k < c->n_walls) {
-      to_device_wall(c->walls[k], &c->P.walls[k], &c->P.wf[k], c->P.wf_v[k]);
+      to_device_wall(c->walls[k], &c->P.walls[k], &c->P.wf[k], c->P.wf_v[k], &c->P.wx[k]);
     } else {
       std::memset(&c->P.walls[k], 0, sizeof(WallDev));
       std::memset(&c->P.wf[k], 0, sizeof(WallF));
+      std::memset(&c->P.wx[k], 0, sizeof(WallX));
+      c->P.wx[k].axis = -1;
       for (int d = 0; d < 3; d++) c->P.wf_v[k][d] = 0.0f;
     }
   }
@@ -945,7 +972,7 @@ dem_status dem_set_instances(dem_ctx* c, const dem_instance* inst, int32_t n_ins
     D.n_walls = I.n_walls;
     for (int w = 0; w < I.n_walls; w++) {
       if (!valid_wall(I.walls[w])) return DEM_ERR_ARG;
-      to_device_wall(I.walls[w], &D.walls[w], &D.wf[w], D.wf_v[w]);
+      to_device_wall(I.walls[w], &D.walls[w], &D.wf[w], D.wf_v[w], &D.wx[w]);
       if (D.walls[w].translates) any_tr = 1;
     }
     for (long long i = lo; i < hi; i++) of[(size_t)i] = k;

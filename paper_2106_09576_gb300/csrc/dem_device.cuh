@@ -83,6 +83,19 @@ struct WallF {     // 32 bytes: the prefilter reads it for every particle
   float p[3], n[3], radius, inner;
 };
 
+// The mixed path's FP32 form of a plane or cylinder whose normal or axis is a coordinate
+// axis (and that does not translate): the point and the radius as hi + lo pairs, so that
+// the overlap comes out of double-float arithmetic as accurately as from FP64, and the
+// rotation in FP32 for the wall's velocity at the contact point.  axis < 0: no such form,
+// the FP64 geometry is used.
+struct WallX {
+  int axis;          // n = sign * e_axis, or -1
+  float sign;
+  float ph[3], pl[3];  // point = ph + pl
+  float rh, rl;        // radius = rh + rl (cylinder)
+  float Om[3], c[3], V[3];
+};
+
 // Material constants of one contact type pair (Table equation_parameters): effective Y
 // and G, -2 sqrt(5/6) beta, sliding and rolling friction; particle-particle (_pp) and
 // particle-wall (_pw).  MatF holds their FP32 copies for the mixed path.
@@ -106,6 +119,7 @@ struct InstDev {
   WallDev walls[kMaxInstWalls];
   WallF wf[kMaxInstWalls];
   float wf_v[kMaxInstWalls][3];   // FP32 translation velocity of translating walls, else 0
+  WallX wx[kMaxInstWalls];
 };
 
 // Device-resident control block: everything that changes from step to step.
@@ -191,6 +205,7 @@ struct Params {
   long long z_sink_key;   // ordered-integer image of z_sink (exact comparison without FP64)
   WallF wf[kMaxWalls];
   float wf_v[kMaxWalls][3];   // FP32 translation velocity of translating walls, else 0
+  WallX wx[kMaxWalls];
   // batch (n_inst > 1): per-instance materials and walls replace md, mf, walls, wf
   int n_inst;
   const InstDev* itab;  // [n_inst]

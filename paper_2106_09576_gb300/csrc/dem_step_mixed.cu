@@ -35,28 +35,128 @@ struct WallOut {
   int hit;
 };
 
+// A particle's FP32 copy unpacked: position as hi + lo, velocity and spin.
+struct OwnF {
+  float xh[3], xl[3], v[3], w[3];
+};
+
+// Geometry of a contact with an axis-aligned plane or cylinder (WallX) in double-float FP32,
+// the same quantities as the FP64 form: normal (from the particle towards the wall), overlap
+// and the contact point's arm from the rotation origin.  The difference x - p is an exact
+// two-sum of the hi + lo pairs; a plane's overlap R - n.(x - p) keeps R - sign s exact near
+// contact; a cylinder's overlap rho - (radius - R) is formed as (rho^2 - Q^2) / (rho + Q),
+// Q = radius - R, with both squares exact double-floats, as the pair overlap is.  Returns 0
+// without contact, 1 with one, 2 if the FP64 form must decide (a particle wider than the
+// cylinder).
+__device__ __forceinline__ int wall_geom_x(const WallX& X, int kind, const OwnF& own, float R, float* nrm, float* dn,
+                                           float* arm) {
+  const int a = X.axis;
+  const float sg = X.sign;
+  float s[3], t[3];
+  for (int d = 0; d < 3; d++) df_diff(X.ph[d], X.pl[d], own.xh[d], own.xl[d], s[d], t[d]);   // x - p
+  if (kind == 0) {
+    const float ov = (R - sg * s[a]) - sg * t[a];
+    if (!(ov > 0.0f)) return 0;
+    for (int d = 0; d < 3; d++) {
+      nrm[d] = d == a ? -sg : 0.0f;
+      // p* = x - (n.(x - p)) n: p on the normal's axis, x on the others
+      arm[d] = (d == a ? X.ph[d] + X.pl[d] : own.xh[d] + own.xl[d]) - X.c[d];
+    }
+    *dn = ov;
+    return 1;
+  }
+  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  float Ah, Al, pe, p2, e2;
+  two_prod(s[b], s[b], Ah, pe);
+  Al = pe + (2.0f * s[b] + t[b]) * t[b];
+  two_prod(s[c], s[c], p2, pe);
+  two_sum(Ah, p2, Ah, e2);
+  Al += e2 + pe + (2.0f * s[c] + t[c]) * t[c];
+  float Qh, Qe;
+  two_sum(X.rh, -R, Qh, Qe);
+  const float Ql = Qe + X.rl;
+  if (!(Qh > 0.0f)) return 2;
+  float Q2, Q2e, Dh, De;
+  two_prod(Qh, Qh, Q2, Q2e);
+  Q2e += 2.0f * Qh * Ql;
+  two_sum(Ah, -Q2, Dh, De);
+  const float D = Dh + (De + (Al - Q2e));
+  if (!(D > 0.0f)) return 0;
+  const float rho = sqrtf(Ah + Al);
+  *dn = D / (rho + (Qh + Ql));
+  const float ir = 1.0f / rho;
+  for (int d = 0; d < 3; d++) {
+    const float u = d == a ? 0.0f : (s[d] + t[d]) * ir;
+    nrm[d] = u;
+    // p* = p + (n.(x - p)) n + radius u: x on the axis, p + radius u across it
+    arm[d] = (d == a ? own.xh[d] + own.xl[d] : (X.ph[d] + X.pl[d]) + (X.rh + X.rl) * u) - X.c[d];
+  }
+  return 1;
+}
+
 template <bool kBatch, bool kExt>
-__device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstDev* I, int k, int i, int cur, double x0,
-                                                   double x1, double x2, float Rif, float mif,
-                                                   unsigned long long mold, const double* Hold, bool init) {
+__device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstDev* I, int k, int i, int cur, float Rif,
+                                                   float mif, unsigned long long mold, const double* Hold, bool init) {
   const Params& P = *Pp;
   const WallDev& Wl = kBatch ? I->walls[k] : P.walls[k];
+  const WallX& Xw = kBatch ? I->wx[k] : P.wx[k];
 
   const MatF& Mt = kBatch ? I->mf : P.mf;
   WallOut o;
   o.hit = 0;
-  double xi[3] = {x0, x1, x2};
-  if (kExt && Wl.translates) {   // a translating wall is handled in its own frame: x - V t
-    const double tw = (double)P.ctl->step * P.dt;
-    for (int d = 0; d < 3; d++) xi[d] = xi[d] - Wl.V[d] * tw;
+  // normal, overlap, v_i - V_wall(p*), w_i - Omega and w_i in FP32
+  float nf[3], dnf, dv[3], dw[3], wif[3];
+  int geo = 2;
+  if (Xw.axis >= 0) {
+    // the particle's FP32 copy, read again here (rare) rather than kept live by the caller
+    const float4* rd = P.render[cur] + 3 * (size_t)i;
+    const float4 q0 = rd[0], q1 = rd[1], q2 = rd[2];
+    const OwnF own = {{q0.x, q0.y, q0.z}, {q0.w, q1.x, q1.y}, {q1.z, q1.w, q2.x}, {q2.y, q2.z, q2.w}};
+    float arm[3];
+    geo = wall_geom_x(Xw, Wl.kind, own, Rif, nf, &dnf, arm);
+    if (geo == 0) return o;
+    if (geo == 1) {
+      const float Vw[3] = {Xw.Om[1] * arm[2] - Xw.Om[2] * arm[1] + Xw.V[0],
+                           Xw.Om[2] * arm[0] - Xw.Om[0] * arm[2] + Xw.V[1],
+                           Xw.Om[0] * arm[1] - Xw.Om[1] * arm[0] + Xw.V[2]};
+      for (int d = 0; d < 3; d++) {
+        dv[d] = own.v[d] - Vw[d];
+        dw[d] = own.w[d] - Xw.Om[d];
+        wif[d] = own.w[d];
+      }
+    }
   }
-  double nrmd[3], dnd, ps[3];   // ps in the wall's frame: p* - c is the same in both frames
-  if (!wall_geom_d(Wl, xi, (double)Rif, nrmd, &dnd, ps)) return o;
-  const int n = P.n;
-  const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
-  double Vw[3];
-  cross3d(Wl.Om, arm, Vw);
-  for (int d = 0; d < 3; d++) Vw[d] += Wl.V[d];
+  if (geo == 2) {
+    // any other wall: FP64 geometry
+    const int n = P.n;
+    double xi[3] = {P.x[cur][i], P.x[cur][n + i], P.x[cur][2 * n + i]};
+    if (kExt && Wl.translates) {   // a translating wall is handled in its own frame: x - V t
+      const double tw = (double)P.ctl->step * P.dt;
+      for (int d = 0; d < 3; d++) xi[d] = xi[d] - Wl.V[d] * tw;
+    }
+    double nrmd[3], dnd, ps[3];   // ps in the wall's frame: p* - c is the same in both frames
+    if (!wall_geom_d(Wl, xi, (double)Rif, nrmd, &dnd, ps)) return o;
+    const double arm[3] = {ps[0] - Wl.c[0], ps[1] - Wl.c[1], ps[2] - Wl.c[2]};
+    double Vw[3];
+    cross3d(Wl.Om, arm, Vw);
+    for (int d = 0; d < 3; d++) Vw[d] += Wl.V[d];
+    for (int d = 0; d < 3; d++) nf[d] = (float)nrmd[d];
+    dnf = (float)dnd;
+    // v_i - V_wall(p*) and w_i - Omega as exact double-float differences
+    for (int d = 0; d < 3; d++) {
+      const double vi = P.v[cur][d * n + i], wi = P.w[cur][d * n + i];
+      float ah, al, bh, bl, s1, t1;
+      split_df(vi, ah, al);
+      split_df(Vw[d], bh, bl);
+      df_diff(bh, bl, ah, al, s1, t1);
+      dv[d] = s1 + t1;
+      split_df(wi, ah, al);
+      split_df(Wl.Om[d], bh, bl);
+      df_diff(bh, bl, ah, al, s1, t1);
+      dw[d] = s1 + t1;
+      wif[d] = d2f_int(wi);
+    }
+  }
   const int bit = kMaxNbr + k;
   double H[3] = {0.0, 0.0, 0.0};
   if ((mold >> bit) & 1ull) {
@@ -64,23 +164,6 @@ __device__ __noinline__ WallOut wall_contact_mixed(const Params* Pp, const InstD
     H[0] = Hold[hcomp(P.n, ro, 0)];
     H[1] = Hold[hcomp(P.n, ro, 1)];
     H[2] = Hold[hcomp(P.n, ro, 2)];
-  }
-  const float nf[3] = {(float)nrmd[0], (float)nrmd[1], (float)nrmd[2]};
-  const float dnf = (float)dnd;
-  // v_i - V_wall(p*) and w_i - Omega as exact double-float differences
-  float dv[3], dw[3], wif[3];
-  for (int d = 0; d < 3; d++) {
-    const double vi = P.v[cur][d * n + i], wi = P.w[cur][d * n + i];
-    float ah, al, bh, bl, s1, t1;
-    split_df(vi, ah, al);
-    split_df(Vw[d], bh, bl);
-    df_diff(bh, bl, ah, al, s1, t1);
-    dv[d] = s1 + t1;
-    split_df(wi, ah, al);
-    split_df(Wl.Om[d], bh, bl);
-    df_diff(bh, bl, ah, al, s1, t1);
-    dw[d] = s1 + t1;
-    wif[d] = d2f_int(wi);
   }
   const float rw[3] = {Rif * wif[0], Rif * wif[1], Rif * wif[2]};
   const float vij[3] = {dv[0] + (rw[1] * nf[2] - rw[2] * nf[1]), dv[1] + (rw[2] * nf[0] - rw[0] * nf[2]),
@@ -286,8 +369,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_step_mixed(const __grid_const
         } else if (!wall_maybe_f(WLs[k].kind, WFs[k], xf, Rif, P.wall_margin)) {
           continue;
         }
-        const WallOut o = wall_contact_mixed<kBatch, kExt>(&P, I, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold,
-                                                     Hold, init);
+        const WallOut o = wall_contact_mixed<kBatch, kExt>(&P, I, k, i, cur, Rif, mif, mold, Hold, init);
         if (!o.hit) continue;
         for (int d = 0; d < 3; d++) {
           Ff[d] += o.F[d];
@@ -401,7 +483,6 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
   const int n = P.n, nact = C->n_act_sorted;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   StepStats st = {0u, 0u, 0u, 0.0f, 0u};
-  const double* X = P.x[cur];
   // read-only in this kernel: the compiler may issue these loads ahead of the stores
   const float4* __restrict__ RD = P.render[cur];
   const float* __restrict__ RAD = P.rad[C->sbuf];
@@ -563,8 +644,7 @@ __global__ void __launch_bounds__(kStepBlock, 6) k_pair_mixed(const __grid_const
         } else if (!wall_maybe_f(WLs[k].kind, WFs[k], xf, Rif, P.wall_margin)) {
           continue;
         }
-        const WallOut o = wall_contact_mixed<kBatch, kExt>(&P, I, k, i, cur, X[i], X[n + i], X[2 * n + i], Rif, mif, mold,
-                                                     Hold, init);
+        const WallOut o = wall_contact_mixed<kBatch, kExt>(&P, I, k, i, cur, Rif, mif, mold, Hold, init);
         if (!o.hit) continue;
         for (int d = 0; d < 3; d++) {
           Ff[d] += o.F[d];
