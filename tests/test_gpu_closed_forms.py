@@ -70,6 +70,28 @@ def test_static_overlap_on_plane_matches_hertz(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_static_overlap_in_a_horizontal_cylinder_matches_hertz(precision):
+    # the sphere rests at the bottom of a drum (axis along y, 8 cm radius, off the origin):
+    # the wall model takes the sphere's own radius as the contact radius, so the overlap is
+    # the plane's, 8e-7 m against a distance from the axis of 8e-2 m -- an FP32 radial
+    # distance alone would be off by ~5e-9 m, 0.6 % of it
+    pm = mat(restitution=0.3)
+    wm = mat(young=5e7, poisson=0.25, restitution=0.3)
+    R = f32(1.5e-3)
+    Rc, x0 = 0.08, 0.013
+    drum = [workloads.cylinder((x0, 0.0, Rc), (0, 1, 0), Rc)]
+    c = cfg(particle=pm, wall=wm, dt=2e-6, domain_lo=(-0.1, -0.1, -0.01), domain_hi=(0.1, 0.1, 0.19))
+    x, v, _, _ = run(precision, c, (x0, 0, R), (0, 0, 0), R, drum, 60000)
+    K = 4.0 / 3.0 * estar(pm, wm) * math.sqrt(R)
+    d_eq = (mass(R) * G / K) ** (2.0 / 3.0)
+    rho = math.hypot(x[0, 0] - x0, x[0, 2] - Rc)
+    err = abs((rho + R - Rc) - d_eq) / d_eq
+    print(f"{precision}: static overlap in the cylinder, relative error {err:.2e}")
+    assert abs(v[0, 2]) < 1e-9 and abs(x[0, 0] - x0) < 1e-9
+    assert err < (1e-6 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("v_rel", [0.1, 2.0])
 def test_restitution_recovers_input_coefficient(precision, v_rel):
     e = 0.7
